@@ -1,0 +1,73 @@
+"""The ChebFD iteration, Sec. 3.1 steps 4-8 - oracle side.
+
+Readings of the paper taken here (the paper leaves them open):
+* residual threshold: eps is relative, a pair converges when
+  ||H v - theta v|| <= eps ||H||, ||H|| = max(|a|, |b|) (Sec. 3.1 step 8);
+* ghost Ritz pairs (Sec. 3.1 step 7, 'discard ... if it remains larger than
+  sqrt(eps)'): from the second iteration on, an in-window pair is a ghost when
+  its residual exceeds sqrt(eps) ||H|| and did not fall by a factor >= 10
+  against the residual of the previous iteration's pair nearest in theta;
+* convergence (step 8a): at least one accepted in-window pair, and every
+  accepted in-window pair below eps ||H||; the window is closed,
+  lam_lo <= theta <= lam_hi;
+* restart (step 8b): the next search block is the full set of Ritz vectors,
+  which spans the same space as the orthonormalised filtered block;
+* search vectors (step 4): SplitMix64 stream 1, column k of n_s, entry 2u-1 at
+  word index i*n_s + k (real) or 2(i*n_s + k) + {0, 1} (complex parts).
+"""
+import numpy as np
+
+from . import coeffs, filter as filt, rng, rr, svqb
+
+
+def search_vectors(seed, D, ns, complex_values):
+    idx = np.arange(D, dtype=np.uint64)[:, None] * np.uint64(ns) + np.arange(ns, dtype=np.uint64)[None, :]
+    if complex_values:
+        re = 2 * rng.uniform(seed, rng.STREAM_SEARCH, 2 * idx) - 1
+        im = 2 * rng.uniform(seed, rng.STREAM_SEARCH, 2 * idx + np.uint64(1)) - 1
+        return re + 1j * im
+    return 2 * rng.uniform(seed, rng.STREAM_SEARCH, idx) - 1
+
+
+def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
+           max_iter=40, filter_fn=None, X0=None, complex_values=None):
+    """Run ChebFD; returns a dict with the accepted pairs and the iteration log.
+
+    ``filter_fn(X)``, when given, replaces the recurrence of Fig. ChebFD by
+    another evaluation of p[H] X (used for diagonal H, where p[H] X = p(lambda) X)."""
+    D = H.shape[0]
+    if complex_values is None:
+        complex_values = np.iscomplexobj(H.data) if hasattr(H, "data") else False
+    alpha, beta = coeffs.scaling(a, b)
+    gc = coeffs.filter_coeffs(a, b, lam_lo, lam_hi, Np, kind, mu)
+    normH = max(abs(a), abs(b))
+    X = search_vectors(seed, D, ns, complex_values) if X0 is None else np.array(X0, copy=True)
+    refill = 0
+    log = []
+    prev = None
+    result = None
+    for it in range(1, max_iter + 1):
+        Y = filter_fn(X) if filter_fn is not None else filt.filter_block(H, alpha, beta, gc, X)
+        Q, rank, refill = svqb.svqb(Y, seed=seed, refill_counter=refill)
+        theta, V, res = rr.rayleigh_ritz(H, Q)
+        inwin = (theta >= lam_lo) & (theta <= lam_hi)
+        ghost = np.zeros_like(inwin)
+        if prev is not None:
+            pth, pres = prev
+            for k in np.nonzero(inwin)[0]:
+                j = int(np.argmin(np.abs(pth - theta[k])))
+                if res[k] > np.sqrt(eps) * normH and not (pres[j] >= 10.0 * res[k]):
+                    ghost[k] = True
+        acc = inwin & ~ghost
+        converged = bool(acc.any()) and bool(np.all(res[acc] <= eps * normH))
+        log.append(dict(iteration=it, rank=rank, in_window=int(inwin.sum()),
+                        ghosts=int(ghost.sum()), accepted=int(acc.sum()),
+                        res_min=float(res[acc].min()) if acc.any() else None,
+                        res_max=float(res[acc].max()) if acc.any() else None))
+        result = dict(theta=theta[acc], V=V[:, acc], res=res[acc], iterations=it,
+                      n_mvm=it * ns * Np, converged=converged, log=log, normH=normH)
+        if converged:
+            break
+        prev = (theta, res)
+        X = V
+    return result

@@ -1,0 +1,406 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks an oracle function against something other than itself: a
+value printed in the paper (fixtures under tests/golden/, each citing its
+table or figure), a closed form, an invariant, brute force on a tiny case, or
+a library routine that the definition reduces to.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.sparse as sp
+
+from oracle import bounds, coeffs, filter as filt, kpm, lattice, quality, rng, rr, sell, solve, svqb
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    out = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                out.append(line.split())
+    return out
+
+
+# ---------------------------------------------------------------- generator
+
+
+def test_splitmix64_known_answers():
+    want = [int(r[0], 16) for r in _rows("splitmix64_seed0.txt")]
+    got = [int(x) for x in rng.words(0, 0, np.arange(len(want)))]
+    assert got == want
+
+
+def test_uniform_range_and_streams_differ():
+    u = rng.uniform(7, 0, np.arange(10000))
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 0.02
+    assert not np.array_equal(rng.words(7, 0, np.arange(8)), rng.words(7, 1, np.arange(8)))
+
+
+# ---------------------------------------------------------------- coefficients
+
+
+@pytest.mark.parametrize("window", [(-0.1, 0.1), (-0.3, 0.05), (0.2, 0.9)])
+def test_window_coefficients_match_defining_integral(window):
+    """c_n = (2 - delta_n0)/pi int_{-1}^{1} W T_n (1-x^2)^(-1/2) dx  (Sec. 2.1),
+    integrated numerically in x = cos(theta) on [a, b] = [-2, 3]."""
+    a, b = -2.0, 3.0
+    lo, hi = window
+    alpha, beta = coeffs.scaling(a, b)
+    c = coeffs.window_cn(a, b, lo, hi, 40)
+    for n in (0, 1, 2, 7, 40):
+        # W((b-a)/2 x + (a+b)/2) is 1 for x in [alpha lo + beta, alpha hi + beta]
+        x0, x1 = alpha * lo + beta, alpha * hi + beta
+        f = lambda x: np.cos(n * np.arccos(x)) / np.sqrt(1 - x * x)
+        val, _ = scipy.integrate.quad(f, x0, x1, limit=200)
+        ref = (2.0 - (n == 0)) / np.pi * val
+        assert abs(c[n] - ref) < 1e-10, (n, c[n], ref)
+
+
+def test_scaling_maps_interval():
+    alpha, beta = coeffs.scaling(-5.5, 5.5)
+    assert alpha * -5.5 + beta == pytest.approx(-1.0) and alpha * 5.5 + beta == pytest.approx(1.0)
+
+
+def test_kernel_factors_special_values():
+    Np = 50
+    for k in coeffs.KERNELS:
+        assert coeffs.kernel_gn(k, Np)[0] == pytest.approx(1.0, abs=1e-14)
+    j = coeffs.kernel_gn("jackson", Np)
+    assert abs(j[Np]) < 1e-14 and abs(j[Np - 1]) < 1e-14
+    f = coeffs.kernel_gn("fejer", Np)
+    assert f[Np] == pytest.approx(1.0 / (Np + 1))
+    l1 = coeffs.kernel_gn("lanczos", Np, mu=1.0)
+    n = np.arange(1, Np + 1)
+    assert np.allclose(l1[1:], np.sinc(n / (Np + 1.0)))
+    assert np.allclose(coeffs.kernel_gn("lanczos", Np, mu=3.0)[1:], l1[1:] ** 3)
+
+
+@pytest.mark.parametrize("kind", ["jackson", "fejer"])
+def test_positive_kernels_have_no_gibbs_overshoot(kind):
+    """Fejer and Jackson are positive kernels (WWAF06): the damped expansion of
+    the window stays inside [0, 1]; the undamped one overshoots (Fig. filters)."""
+    gc = coeffs.filter_coeffs(-1, 1, -0.01, 0.01, 200, kind)
+    x = np.linspace(-1, 1, 20001)
+    p = coeffs.eval_poly(gc, x)
+    assert p.min() > -1e-12 and p.max() < 1 + 1e-12
+    p_none = coeffs.eval_poly(coeffs.filter_coeffs(-1, 1, -0.01, 0.01, 200, "none"), x)
+    assert p_none.min() < -0.01
+
+
+def test_filter_is_about_one_inside_window():
+    """p ~ 1 inside a wide window (Sec. 2.2) - pins the sign reading of c_n."""
+    gc = coeffs.filter_coeffs(-1, 1, -0.2, 0.2, 400, "lanczos")
+    assert coeffs.eval_poly(gc, np.array([0.0]))[0] == pytest.approx(1.0, abs=1e-3)
+
+
+# ---------------------------------------------------------------- filter
+
+
+def test_filter_on_diagonal_matches_cos_closed_form():
+    """T_n(cos t) = cos(n t) (Sec. 2.1): for diagonal H and unit vectors the
+    filtered entry i is sum_n gc_n cos(n arccos(alpha l_i + beta))."""
+    lam = np.linspace(-1.9, 2.9, 300)
+    H = sp.diags(lam).tocsr()
+    a, b = -2.0, 3.0
+    alpha, beta = coeffs.scaling(a, b)
+    gc = coeffs.filter_coeffs(a, b, -0.3, 0.4, 250, "lanczos")
+    X = np.eye(300)[:, :40] + 0.5 * np.eye(300)[:, 100:140]
+    Y = filt.filter_block(H, alpha, beta, gc, X)
+    th = np.arccos(alpha * lam + beta)
+    n = np.arange(len(gc))
+    p = np.cos(np.outer(th, n)) @ gc
+    assert np.abs(Y - p[:, None] * X).max() <= 1e-13 * np.abs(gc).sum()
+
+
+def test_filter_matches_dense_spectral_form_on_small_lattice():
+    """p[H] X = V p(Lambda) V^H X with V, Lambda from a dense eigensolver."""
+    rp, c, v = lattice.topi_csr(3, 4, 3, W=1.3, seed=11)
+    H = lattice.to_scipy(rp, c, v)
+    lam, V = np.linalg.eigh(H.toarray())
+    a, b = lam[0] - 0.1, lam[-1] + 0.1
+    alpha, beta = coeffs.scaling(a, b)
+    gc = coeffs.filter_coeffs(a, b, -0.4, 0.4, 120, "jackson")
+    rs = np.random.default_rng(3)
+    X = rs.standard_normal((H.shape[0], 5)) + 1j * rs.standard_normal((H.shape[0], 5))
+    Y = filt.filter_block(H, alpha, beta, gc, X)
+    p = coeffs.eval_poly(gc, alpha * lam + beta)
+    ref = V @ (p[:, None] * (V.conj().T @ X))
+    assert np.linalg.norm(Y - ref) <= 1e-12 * np.linalg.norm(X)
+
+
+def test_moments_on_diagonal_and_doubling_identities():
+    lam = np.linspace(-0.95, 0.97, 64)
+    H = sp.diags(lam).tocsr()
+    rs = np.random.default_rng(0)
+    X = rs.standard_normal((64, 3))
+    mu = filt.moments(H, 1.0, 0.0, X, 30)
+    th = np.arccos(lam)
+    ref = np.array([(X * X * np.cos(n * th)[:, None]).sum(axis=0) for n in range(30)])
+    assert np.allclose(mu, ref, atol=1e-12)
+    T = filt.chebyshev_vectors(H, 1.0, 0.0, X, 14)
+    for n in range(1, 14):
+        assert np.allclose(mu[2 * n], 2 * (T[n] * T[n]).sum(0) - mu[0], atol=1e-11)
+        assert np.allclose(mu[2 * n + 1], 2 * (T[n + 1] * T[n]).sum(0) - mu[1], atol=1e-11)
+
+
+# ---------------------------------------------------------------- lattices
+
+
+def test_topi_structure_hermitian_and_clean_spectrum():
+    rp, c, v = lattice.topi_csr(4, 4, 6, W=0.0)
+    assert np.all(np.diff(rp) == 13)                     # N_nzr = 13 (Sec. 4)
+    for r in range(0, len(rp) - 1, 37):
+        assert np.all(np.diff(c[rp[r]:rp[r + 1]]) > 0)
+    H = lattice.to_scipy(rp, c, v)
+    assert (H - H.conj().T).count_nonzero() == 0          # bitwise Hermitian
+    e = np.linalg.eigvalsh(H.toarray())
+    assert np.abs(e - lattice.topi_clean_spectrum(4, 4, 6)).max() < 1e-12
+    assert np.sum(np.abs(e) < 1e-12) == 12                # Dirac points perm(0,0,pi)
+    assert e.max() == pytest.approx(4.0)                  # m + 3t
+
+
+def test_topi_disorder_chiral_symmetry():
+    rp, c, v = lattice.topi_csr(3, 3, 4, W=2.0, seed=5)
+    H = lattice.to_scipy(rp, c, v)
+    assert (H - H.conj().T).count_nonzero() == 0
+    e = np.linalg.eigvalsh(H.toarray())
+    assert np.abs(e + e[::-1]).max() < 1e-12              # spec(H) = -spec(H)
+    V = lattice.disorder(5, 36, 2.0)
+    assert V.min() >= -1.0 and V.max() < 1.0
+    d = H.diagonal().real
+    assert np.array_equal(d[0::4], 1.0 + V) and np.array_equal(d[2::4], -(1.0 + V))
+
+
+def test_topi_small_lattice_duplicates_summed():
+    rp, c, v = lattice.topi_csr(2, 2, 2, W=0.3, seed=1)
+    H = lattice.to_scipy(rp, c, v)
+    assert (H - H.conj().T).count_nonzero() == 0
+    big = lattice.to_scipy(*lattice.topi_csr(2, 2, 2, W=0.3, seed=1))
+    # with edge 2, +e_j and -e_j reach the same site: T_j + T_j^dagger = -t Gamma1
+    assert np.allclose(H.toarray()[0, 4 * 1 + 0], -1.0)
+    assert np.array_equal(H.toarray(), big.toarray())
+
+
+def test_graphene_structure_and_clean_spectrum():
+    rp, c, v = lattice.graphene_csr(6, 9, W=0.0)
+    assert np.all(np.diff(rp) == 4)
+    H = lattice.to_scipy(rp, c, v)
+    assert (H - H.T).count_nonzero() == 0
+    e = np.linalg.eigvalsh(H.toarray())
+    assert np.abs(e - lattice.graphene_clean_spectrum(6, 9)).max() < 1e-12
+    rp, c, v = lattice.graphene_csr(5, 5, W=1.0, seed=2)
+    d = lattice.to_scipy(rp, c, v).diagonal()
+    assert d.min() >= -0.5 and d.max() < 0.5
+
+
+# ---------------------------------------------------------------- SELL
+
+
+@pytest.mark.parametrize("C,sigma", [(1, 1), (4, 1), (4, 8), (32, 64), (3, 5)])
+def test_sell_round_trip_and_sorting(C, sigma):
+    rs = np.random.default_rng(C * 100 + sigma)
+    n = 101
+    lens = rs.integers(0, 9, n)
+    rowptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    col = np.concatenate([np.sort(rs.choice(n, l, replace=False)) for l in lens]).astype(np.int32)
+    val = rs.standard_normal(rowptr[-1])
+    S = sell.sell_from_csr(rowptr, col, val, C, sigma)
+    rows = sell.sell_to_dense_rows(S)
+    for r in range(n):
+        got = rows[r][:lens[r]]
+        assert [g[0] for g in got] == list(col[rowptr[r]:rowptr[r + 1]])
+        assert [g[1] for g in got] == list(val[rowptr[r]:rowptr[r + 1]])
+        assert all(p[0] == r and p[1] == 0 for p in rows[r][lens[r]:])
+    perm = S["perm"]
+    assert sorted(perm) == list(range(n))
+    for w0 in range(0, n, sigma):
+        win = perm[w0:w0 + sigma]
+        assert sorted(win) == list(range(w0, min(w0 + sigma, n)))
+        key = [(-lens[r], r) for r in win]
+        assert key == sorted(key)
+    assert S["chunk_ptr"][-1] == sum(S["chunk_len"]) * C
+
+
+# ---------------------------------------------------------------- filter quality
+
+
+def test_fig_polyeff1_optimal_degrees():
+    for kind, want in _rows("fig_polyeff1.txt"):
+        want = int(want)
+        n_opt, _ = quality.optimal_Np(1e-3, 1e-3, kind=kind, n_lo=int(0.8 * want), n_hi=int(1.25 * want))
+        assert abs(n_opt - want) <= 0.02 * want, (kind, n_opt, want)
+
+
+def test_tab_lanczoskernel_scaling_constants():
+    rows = _rows("tab_lanczoskernel.txt")
+    for c, N0, eta0 in rows[::3]:
+        c, N0, eta0 = float(c), float(N0), float(eta0)
+        n_opt, e_opt = quality.optimal_Np(1e-3, 1e-3, c=c, n_lo=int(800 * N0), n_hi=int(1250 * N0))
+        assert abs(n_opt / 1000.0 - N0) <= 0.02 * N0, (c, n_opt)
+        assert abs(e_opt / 1000.0 - eta0) <= 0.02 * eta0, (c, e_opt)
+
+
+def test_tab_num_optimal_degree_quality_and_effort():
+    for dos, NS, dpd, Np, eta, est, num, nit, star in _rows("tab_num.txt")[::2]:
+        NS, dpd, Np, eta, est = int(NS), float(dpd), int(Np), float(eta), float(est)
+        delta = 2.5e-3 if dos == "flat" else 0.05
+        margin = quality.margin_flat(NS, 100) if dos == "flat" else quality.margin_linear(NS, 100)
+        assert abs(margin - dpd) <= 0.006
+        # the table's N_p^opt follow from its printed (rounded) delta'/delta
+        n_opt, e_opt = quality.optimal_Np(delta, dpd * delta, n_lo=int(0.8 * Np), n_hi=int(1.25 * Np) + 2)
+        assert abs(n_opt - Np) <= max(0.02 * Np, 2), (dos, NS, n_opt, Np)
+        assert abs(e_opt - eta) <= 0.02 * eta + 1, (dos, NS, e_opt, eta)
+        # estimate column: N_MVM = eta N_S (-log10 eps), eps = 1e-12
+        assert abs(e_opt * NS * 12 / 1e6 - est) <= 0.03 * est + 0.01
+
+
+def test_effort_model_linear_minimum_at_four_NT():
+    NS = np.linspace(110, 900, 2000)
+    f = quality.effort_linear(2.58, 1.0, 0.05, 100, NS)
+    assert abs(NS[np.argmin(f)] - 400) < 2
+    assert f.min() == pytest.approx(4 * 2.58 / 0.05 * 100, rel=1e-4)
+    g = quality.effort_flat(2.58, 1.0, 0.0025, 100, NS)
+    assert np.all(np.diff(g) < 0)
+
+
+def test_topi_effort_estimate_sec53():
+    """Sec. 5.2: minimal effort 1.06e6 spMVMs for [a,b] = [-5.5, 5.5],
+    I_T = [-0.06, 0.06], eps = 1e-9 (linear DOS, N_S = 4 N_T); the figure
+    follows from the DOS estimate N_T ~ 124 quoted there (not the final 144)."""
+    f = quality.effort_linear(2.58, 5.5, 0.06, 124, 4 * 124) * 9
+    assert f == pytest.approx(1.06e6, rel=0.01)
+
+
+# ---------------------------------------------------------------- search-space weight
+
+
+def test_fig_filtermatrix_weight_bound():
+    """Sec. 2.2: D = 1000, I_T = [-0.01, 0.01], N_S = 50, N_p = 200, Lanczos mu=2:
+    after one filter step 1 - w_i <= ~1.5e-5 inside the target interval."""
+    D = 1000
+    lam = lattice.flat_dos_eigs(D)
+    gc = coeffs.filter_coeffs(-1, 1, -0.01, 0.01, 200, "lanczos")
+    p = coeffs.eval_poly(gc, lam)
+    inw = np.abs(lam) <= 0.01
+    assert inw.sum() == 10
+    worst = []
+    for seed in range(5):
+        X = solve.search_vectors(seed, D, 50, False)
+        Q, _, _ = svqb.svqb(p[:, None] * X)
+        w = np.sqrt((np.abs(Q) ** 2).sum(axis=1))     # eigenvectors are unit vectors
+        worst.append((1 - w[inw]).max())
+    assert max(worst) <= 1e-4
+    assert np.median(worst) <= 3e-5
+
+
+# ---------------------------------------------------------------- KPM, bounds, SVQB, RR
+
+
+def test_kpm_trace_exact_on_diagonal_and_count():
+    lam = lattice.flat_dos_eigs(2000)
+    H = sp.diags(lam).tocsr()
+    mu = kpm.moments(H, 1.0, 0.0, 64, 3, seed=1, complex_values=False)
+    ref = np.array([np.mean(np.cos(n * np.arccos(lam))) for n in range(64)])
+    assert np.allclose(mu, ref, atol=1e-13)               # |r_i| = 1: exact trace
+    cnt = kpm.count_in_window(kpm.moments(H, 1.0, 0.0, 512, 1, 1, False), 2000, -1, 1, -0.2, 0.2)
+    assert abs(cnt - 400) < 8
+
+
+def test_kpm_count_on_lattice_against_dense():
+    rp, c, v = lattice.topi_csr(4, 4, 4, W=1.0, seed=4)
+    H = lattice.to_scipy(rp, c, v)
+    e = np.linalg.eigvalsh(H.toarray())
+    a, b = e[0] - 0.05, e[-1] + 0.05
+    alpha, beta = coeffs.scaling(a, b)
+    mu = kpm.moments(H, alpha, beta, 256, 16, seed=3, complex_values=True)
+    assert mu[0] == pytest.approx(1.0, abs=1e-12)
+    cnt = kpm.count_in_window(mu, H.shape[0], a, b, -1.5, 1.5)
+    assert abs(cnt - np.sum(np.abs(e) <= 1.5)) < 12
+
+
+@pytest.mark.parametrize("gen", ["topi", "graphene"])
+def test_lanczos_bounds_enclose_spectrum(gen):
+    if gen == "topi":
+        H = lattice.to_scipy(*lattice.topi_csr(5, 4, 4, W=1.5, seed=2))
+    else:
+        H = lattice.to_scipy(*lattice.graphene_csr(12, 10, W=1.0, seed=2))
+    e = np.linalg.eigvalsh(H.toarray())
+    a, b = bounds.lanczos_bounds(H, 30, seed=1)
+    assert a <= e[0] and b >= e[-1]
+    assert (b - a) <= 1.06 * (e[-1] - e[0])
+    g_lo, g_hi = bounds.gershgorin(H)
+    assert g_lo <= a and b <= g_hi
+
+
+def test_svqb_orthonormal_same_span_and_refill():
+    rs = np.random.default_rng(1)
+    Y = rs.standard_normal((500, 20)) + 1j * rs.standard_normal((500, 20))
+    Y[:, 3] *= 1e-6
+    Q, rank, cnt = svqb.svqb(Y)
+    assert rank == 20 and cnt == 0
+    assert np.abs(Q.conj().T @ Q - np.eye(20)).max() < 1e-12
+    # same span: projecting Y onto span(Q) reproduces Y
+    assert np.linalg.norm(Y - Q @ (Q.conj().T @ Y)) < 1e-10 * np.linalg.norm(Y)
+    Z = np.concatenate([Y[:, :10], Y[:, :10] @ rs.standard_normal((10, 6))], axis=1)
+    Q2, rank2, cnt2 = svqb.svqb(Z, seed=3)
+    assert rank2 == 10 and cnt2 == 6 and Q2.shape == (500, 16)
+    assert np.abs(Q2.conj().T @ Q2 - np.eye(16)).max() < 1e-12
+    assert np.linalg.norm(Z[:, :10] - Q2 @ (Q2.conj().T @ Z[:, :10])) < 1e-9 * np.linalg.norm(Z)
+
+
+def test_rayleigh_ritz_exact_on_invariant_subspace():
+    H = lattice.to_scipy(*lattice.topi_csr(3, 3, 3, W=0.8, seed=9))
+    lam, V = np.linalg.eigh(H.toarray())
+    rs = np.random.default_rng(2)
+    M = np.linalg.qr(rs.standard_normal((12, 12)) + 1j * rs.standard_normal((12, 12)))[0]
+    Y = V[:, 40:52] @ M                                   # rotated invariant subspace
+    theta, Vr, res = rr.rayleigh_ritz(H, Y)
+    assert np.allclose(theta, lam[40:52], atol=1e-12)
+    assert res.max() < 1e-12
+    assert np.allclose(res, rr.residual_norms(H, Vr, theta), atol=1e-13)
+
+
+# ---------------------------------------------------------------- whole iteration
+
+
+@pytest.mark.parametrize("dos,NS,Np,want", [("linear", 200, 303, 5), ("flat", 200, 2500, 5),
+                                            ("linear", 400, 124, 6), ("flat", 300, 1258, 6)])
+def test_tab_num_iteration_counts(dos, NS, Np, want):
+    """Tab. num: ChebFD on D = 40000 diagonal matrices finds all N_T = 100 target
+    eigenpairs in N_iter iterations (+-1: the stars of the table).  For diagonal
+    H, p[H] X = p(lambda) X exactly, which replaces the recurrence here."""
+    D = 40000
+    lam = lattice.flat_dos_eigs(D) if dos == "flat" else lattice.linear_dos_eigs(D)
+    delta = 2.5e-3 if dos == "flat" else 0.05
+    H = sp.diags(lam).tocsr()
+    p = coeffs.eval_poly(coeffs.filter_coeffs(-1, 1, -delta, delta, Np, "lanczos"), lam)
+    r = solve.chebfd(H, -1.0, 1.0, -delta, delta, NS, Np, 1e-12,
+                     filter_fn=lambda X: p[:, None] * X, complex_values=False)
+    assert r["converged"] and abs(r["iterations"] - want) <= 1
+    exact = np.sort(lam[np.abs(lam) <= delta])
+    assert len(exact) == 100 and len(r["theta"]) == 100
+    assert np.abs(np.sort(r["theta"]) - exact).max() < 1e-12
+
+
+def test_chebfd_small_topi_against_dense():
+    """The smallest insulator workload: 8x8x8x4 (N = 2048), W = 0.5, window
+    [-0.1, 0.1], n_s = 64, N_p = 200, Jackson; all window eigenvalues of the
+    dense eigensolver within 1e-10 ||H||, residuals <= 1e-9 ||H||."""
+    H = lattice.to_scipy(*lattice.topi_csr(8, 8, 8, t=1.0, m=1.0, W=0.5, seed=0))
+    a, b = bounds.lanczos_bounds(H, 30, seed=0)
+    e = np.linalg.eigvalsh(H.toarray())
+    r = solve.chebfd(H, a, b, -0.1, 0.1, 64, 200, 1e-9, kind="jackson", seed=0)
+    ew = e[np.abs(e) <= 0.1]
+    assert r["converged"] and len(r["theta"]) == len(ew) > 0
+    assert np.abs(np.sort(r["theta"]) - ew).max() <= 1e-10 * r["normH"]
+    assert r["res"].max() <= 1e-9 * r["normH"]
+    assert np.abs(r["V"].conj().T @ r["V"] - np.eye(len(ew))).max() < 1e-12
+    th = np.sort(r["theta"])
+    assert np.abs(th + th[::-1]).max() < 1e-10           # chiral +- pairing
