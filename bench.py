@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Throughput of the ChebFD polynomial filter (Fig. ChebFD) on GB300.
+
+Workload: the 64x64x32x4 topological insulator (N = 524288, W = 1.0, seed 1),
+a search space of n_s = 256 vectors filtered in four row-major blocks of
+n_b = 64, complex64 recurrence with FP32 accumulation, Lanczos kernel (mu = 2),
+central window [-delta, delta] holding ~100 eigenpairs (oracle KPM, frozen in
+tests/golden/topi_64x64x32_window.txt), N_p from the Lanczos-kernel scaling
+N_p = N_0 S_w / delta' with N_0 = 6.23 and delta' = delta (N_S = 4 N_T, linear DOS).
+
+One step = one application p[H] X of the degree-N_p filter to the whole
+search block.  metric = filter row-vector updates per second
+(N * n_s * N_p / t).  Prints one JSON line (rank 0).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WINDOW_FILE = os.path.join(ROOT, "tests", "golden", "topi_64x64x32_window.txt")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "cheb_step_c64_nb64_topi64x64x32.txt")
+METRIC = "filter row-vector updates/s (N * n_s * N_p / t)"
+UNIT = "row-vector updates/s"
+N0_LANCZOS = 6.23
+
+
+def load_window():
+    vals = {}
+    with open(WINDOW_FILE) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals["a"], vals["b"], vals["delta"]
+
+
+def workload_params(args):
+    """N_p by the rule of Sec. 3.1 step 3 / Sec. 2.4: the search-interval margin
+    delta' follows from N_S = 256 and the KPM count N_T ~ 100 for the linear DOS
+    of the insulator (delta'/delta = sqrt(N_S/N_T) - 1), and
+    N_p = N_0 S_w / delta' with N_0 = 6.23 (Tab. lanczoskernel, centre)."""
+    from paper_1510_04895_gb300 import workloads
+    w = dict(workloads.TOPI_MEDIUM)
+    a, b, delta = load_window()
+    S_w = 0.5 * (b - a)
+    margin = (np.sqrt(w["ns"] / 100.0) - 1.0) * delta
+    Np = args.Np or int(round(N0_LANCZOS * S_w / margin))
+    return w, a, b, delta, Np
+
+
+def read_traffic():
+    """DRAM bytes per launch of the fused step from the committed ncu summary."""
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            for line in f:
+                if line.startswith("traffic_bytes_per_launch"):
+                    return float(line.split()[1])
+    except OSError:
+        pass
+    return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("CHEBFD_BENCH_BACKEND", "nccl")
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier_max(world, value):
+    """Barrier across ranks and the maximum of a host float."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ CPU legs
+
+
+def oracle_sample(w, a, b, delta, steps_per_sample, nb=64, seed=0):
+    """Time the oracle's FP64 filter recurrence on one nb-wide block of the
+    same matrix: returns (row-vector updates/s, seconds, description)."""
+    from oracle import coeffs, filter as ofilt, lattice
+    from paper_1510_04895_gb300 import workloads
+    Ho = lattice.to_scipy(*lattice.topi_csr(w["Lx"], w["Ly"], w["Lz"], t=w["t"], m=w["m"],
+                                            W=w["W"], seed=w["seed"]))
+    alpha, beta = coeffs.scaling(a, b)
+    gc = coeffs.filter_coeffs(a, b, -delta, delta, steps_per_sample, "lanczos")
+    X = workloads.random_block(seed, Ho.shape[0], nb, True)
+    t0 = time.perf_counter()
+    ofilt.filter_block(Ho, alpha, beta, gc, X)
+    dt = time.perf_counter() - t0
+    units = Ho.shape[0] * nb * steps_per_sample
+    desc = ("oracle FP64 complex128 filter, %d Chebyshev steps on one %d-vector block of the "
+            "N=%d matrix (scipy CSR product, single thread)" % (steps_per_sample, nb, Ho.shape[0]))
+    return units / dt, dt, desc
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    w, a, b, delta, Np = workload_params(args)
+    samples = []
+    for i in range(args.warmup + args.steps):
+        v, dt, desc = oracle_sample(w, a, b, delta, 2, seed=i)
+        if i >= args.warmup:
+            samples.append((v, dt))
+    value = statistics.median(v for v, _ in samples)
+    ms = 1e3 * statistics.median(dt for _, dt in samples)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": "topi 64x64x32x4 (N=524288) W=1.0 seed 1, n_b=64, window "
+                                   "[-%.6g, %.6g]" % (delta, delta)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1510_04895_gb300 as pkg
+    from paper_1510_04895_gb300 import workloads
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w, a, b, delta, Np = workload_params(args)
+    ns, nb = w["ns"], args.nb
+    H = pkg.chebfd_matrix_create_lattice("topi", w["Lx"], w["Ly"], w["Lz"], t=w["t"], m=w["m"],
+                                         W=w["W"], seed=w["seed"], sell_C=args.sell_C,
+                                         also_single=True)
+    N = H.n
+    alpha, beta = 2.0 / (b - a), (a + b) / (a - b)
+    gc = pkg.chebfd_window_coeffs(a, b, -delta, delta, Np, "lanczos", 2.0)
+    cdt = torch.complex64 if args.precision == "c64" else torch.complex128
+    X = torch.empty((N, ns), dtype=cdt, device=dev)
+    pkg.chebfd_random_block(X, col0=0, ns_total=ns, seed=rank)
+    # the library splits the 256 columns into row-major panels of n_b
+    stream = torch.cuda.current_stream()
+
+    def step():
+        pkg.chebfd_filter_block(H, alpha, beta, gc, X)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t_dev = e0.elapsed_time(e1) / 1e3
+    barrier(world)
+    t_max = barrier_max(world, t_dev)
+    units_rank = N * ns * Np * args.steps
+    value = world * units_rank / t_max
+    launches = args.steps * ((ns + nb - 1) // nb) * Np
+
+    # ---- dominant kernel alone: the fused Chebyshev step (n_b = 64) ----------
+    U = torch.empty((N, nb), dtype=cdt, device=dev)
+    Wv = torch.empty_like(U)
+    Y = torch.empty_like(U)
+    pkg.chebfd_random_block(U, ns_total=nb, seed=11)
+    pkg.chebfd_random_block(Wv, ns_total=nb, seed=12)
+    Y.zero_()
+    for _ in range(5):
+        pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, U, Wv, Y)
+    reps = 50
+    torch.cuda.synchronize()
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for i in range(reps):
+        if i % 2 == 0:
+            pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, U, Wv, Y)
+        else:
+            pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, Wv, U, Y)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    t_launch = k0.elapsed_time(k1) / 1e3 / reps
+    S_v = 8 if cdt == torch.complex64 else 16
+    S_d = S_v
+    nnz_row = 13
+    bytes_launch = N * (nnz_row * (S_d + 4) + 5 * nb * S_v)
+    peaks, peak_kind = measured_peaks()
+    achieved = bytes_launch / t_launch / 1e9
+    traffic = read_traffic() if cdt == torch.complex64 and nb == 64 else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "kernel": "cheb_step_kernel (MODE_STEP, %s, n_b=%d)" % (args.precision, nb),
+            "bytes_per_launch": bytes_launch, "launch_us": t_launch * 1e6,
+            "peak_kind": peak_kind + " (burst copy)"}
+
+    # ---- end to end through the C ABI with host buffers ------------------------
+    Xh = torch.empty((N, ns), dtype=cdt, pin_memory=True)
+    Xh.copy_(X.cpu())
+    Xd = torch.empty_like(X)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_steps = max(1, min(args.steps, 3))
+    for _ in range(e_steps):
+        Xd.copy_(Xh, non_blocking=True)
+        pkg.chebfd_filter_block(H, alpha, beta, gc, Xd)
+        Xh.copy_(Xd, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / e_steps
+    t_e2e = barrier_max(world, t_e2e)
+    e2e = {"value": world * N * ns * Np / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": X.numel() * X.element_size(),
+           "d2h_bytes_per_step": X.numel() * X.element_size()}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": args.precision, "data": "synthetic",
+           "config": {"workload": "topi 64x64x32x4 (N=524288) W=1.0 seed 1", "n_s": ns, "n_b": nb,
+                      "N_p": Np, "kernel": "lanczos mu=2",
+                      "window": [-delta, delta], "spectral_interval": [a, b],
+                      "sell_C": args.sell_C,
+                      "l2": "inputs larger than L2 (search block %.2f GB)" % (
+                          X.numel() * X.element_size() / 1e9),
+                      "parallelism": "independent search blocks per GPU (no collective)"},
+           "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+           "clocks": clk.summary(),
+           "hbm_gbs_filter_region": bytes_launch * launches / t_max / 1e9}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, desc = oracle_sample(w, a, b, delta, args.cpu_steps)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": desc, "seconds": dt}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--nb", type=int, default=64)
+    p.add_argument("--precision", default="c64", choices=["c64", "c128"])
+    p.add_argument("--Np", type=int, default=0)
+    p.add_argument("--sell-C", dest="sell_C", type=int, default=1)
+    p.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=8)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    args = p.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,343 @@
+/*
+ * chebfd.h - C ABI of the GB300 (sm_103a) Chebyshev filter diagonalization
+ * library libchebfd.so.
+ *
+ * Method: Pieper, Kreutzer, Alvermann, Galgon, Fehske, Hager, Lang, Wellein,
+ * "High-performance implementation of Chebyshev filter diagonalization for
+ * interior eigenvalue computations" (arXiv 1510.04895).  Problem statement
+ * (Sec. 2): given a sparse Hermitian H, find the eigenpairs (lambda, v) with
+ * lambda in [lam_lo, lam_hi] and ||H v - lambda v|| <= eps.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns chebfd_status; CHEBFD_OK (0) is success.  No C++
+ *    exception crosses the ABI.  chebfd_last_error() returns a thread-local
+ *    message describing the last failure of the calling thread.
+ *  - Ownership: the caller owns every pointer it passes in and keeps it alive
+ *    for the duration of the call (and, for device buffers used by work queued
+ *    on `stream`, until that work has completed).  The library owns the opaque
+ *    handles (chebfd_matrix, chebfd_result) and frees them in *_destroy.
+ *  - Block vectors are N x nb, ROW-MAJOR (interleaved: row i, vector k at
+ *    X[i*ld + k], Sec. 4 "storage of block vectors in row major order"),
+ *    resident in device memory, with ld >= nb in elements.  The base pointer,
+ *    ld*element_size and nb*element_size must be multiples of 16 bytes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is queued on it; a call returns without waiting
+ *    unless its comment says that it synchronizes.
+ *  - Scalars: chebfd_dtype names the element type of vectors and matrix
+ *    values.  A complex H (insulator) takes C128/C64 vectors, a real H
+ *    (graphene, diagonal) takes R64/R32 vectors.
+ */
+#ifndef CHEBFD_H
+#define CHEBFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHEBFD_ABI_VERSION 1
+
+typedef enum chebfd_status {
+    CHEBFD_OK = 0,
+    CHEBFD_EINVAL = 1,       /* bad argument (null pointer, size, alignment, dtype) */
+    CHEBFD_ENOMEM = 2,       /* device or host allocation failed */
+    CHEBFD_ECUDA = 3,        /* a CUDA runtime / cuBLAS / cuSOLVER call failed */
+    CHEBFD_ENUMERIC = 4,     /* NaN, or the recurrence diverged: spec(H) not inside [a,b] */
+    CHEBFD_ENOCONV = 5,      /* iteration limit reached before convergence */
+    CHEBFD_ETIMEOUT = 6,     /* a bounded device-side wait gave up */
+    CHEBFD_EUNSUPPORTED = 7  /* valid request this build does not implement */
+} chebfd_status;
+
+typedef enum chebfd_dtype {
+    CHEBFD_R64 = 0,   /* double */
+    CHEBFD_C128 = 1,  /* complex double, (re, im) interleaved */
+    CHEBFD_R32 = 2,   /* float */
+    CHEBFD_C64 = 3    /* complex float, (re, im) interleaved */
+} chebfd_dtype;
+
+/* Damping kernels g_n of Tab. Kernel (Sec. 2.1); NONE is g_n = 1 (Sec. 2.3). */
+typedef enum chebfd_kernel {
+    CHEBFD_KERNEL_NONE = 0,
+    CHEBFD_KERNEL_FEJER = 1,
+    CHEBFD_KERNEL_JACKSON = 2,
+    CHEBFD_KERNEL_LANCZOS = 3
+} chebfd_kernel;
+
+typedef enum chebfd_lattice_kind {
+    CHEBFD_LATTICE_TOPI = 0,     /* 3D topological insulator, Eq. Ham form (Sec. 5.1) */
+    CHEBFD_LATTICE_GRAPHENE = 1  /* 2D honeycomb lattice with onsite disorder (Sec. 5.4) */
+} chebfd_lattice_kind;
+
+/* Description of a generated lattice Hamiltonian.
+ *  TOPI: Lx*Ly*Lz sites, 4 orbitals, row = 4*(x + Lx*(y + Ly*z)) + orbital,
+ *    onsite (m + V_s) Gamma1, hopping T_j = -(t/2)(Gamma1 - i Gamma_{j+1}) from
+ *    site s to s+e_j plus Hermitian conjugate, periodic; 13 entries per row
+ *    (N_nzr = 13, Sec. 4).  Gamma1 = sz(x)s0, Gamma2 = sx(x)sx,
+ *    Gamma3 = sx(x)sy, Gamma4 = sx(x)sz.
+ *  GRAPHENE: Lx*Ly cells, row = 2*(i + Lx*j) + sublattice, hopping -t to the
+ *    three nearest neighbours, onsite V; 4 entries per row (N_nzr = 4, Sec. 4).
+ *    Lz and m are ignored.
+ *  Disorder V = W*(u - 1/2), u = top 53 bits of the SplitMix64 word number
+ *  `index` (site for TOPI, row for GRAPHENE) of the generator started at state
+ *  seed*256 + 0, times 2^-53.  Columns ascend within a row; coinciding entries
+ *  (edges of length <= 2) are summed in the order onsite, +x, -x, +y, -y, +z, -z.
+ *  Values are generated in FP64 (C128 for TOPI, R64 for GRAPHENE). */
+typedef struct chebfd_lattice_desc {
+    int32_t kind;        /* chebfd_lattice_kind */
+    int32_t Lx, Ly, Lz;  /* lattice edges, each >= 1 */
+    double t, m, W;      /* hopping, mass (TOPI), disorder strength */
+    uint64_t seed;       /* disorder seed, < 2^56 */
+    int32_t sell_C;      /* SELL chunk height C in {1,2,4,8,16,32} */
+    int32_t sell_sigma;  /* SELL sorting window sigma >= 1 */
+    int32_t also_single; /* nonzero: also keep a C64 / R32 copy of the values */
+    int32_t reserved;
+} chebfd_lattice_desc;
+
+typedef struct chebfd_matrix chebfd_matrix;
+
+typedef struct chebfd_matrix_info {
+    int64_t n;            /* dimension D */
+    int64_t nnz;          /* stored entries without SELL padding */
+    int64_t nnz_padded;   /* SELL slots = chunk_ptr[nchunks] */
+    int64_t nchunks;      /* ceil(n / C) */
+    int32_t C, sigma;     /* SELL-C-sigma parameters */
+    int32_t max_row_len;
+    int32_t is_complex;   /* values C128 (and C64) if nonzero, else R64 (and R32) */
+    int32_t has_single;   /* a single-precision copy of the values exists */
+    int32_t reserved;
+} chebfd_matrix_info;
+
+/* ------------------------------------------------------------------ basics */
+
+int chebfd_abi_version(void);
+const char* chebfd_last_error(void);
+const char* chebfd_status_string(chebfd_status s);
+
+/* ----------------------------------------------------------- matrix (D1) */
+
+/* Build the device SELL-C-sigma matrix (Sec. 4: SELL-32-1 for one vector,
+ * SELL-1-1 for blocks; format of Kreutzer et al. 2014) from a HOST CSR.
+ * rowptr[n+1] (int64, rowptr[0] = 0), col[rowptr[n]] (int32, 0 <= col < n),
+ * val[rowptr[n]] of dtype val_dtype in {R64, C128}; the matrix must be
+ * Hermitian (not checked).  Rows are stably sorted by decreasing length inside
+ * windows of sell_sigma rows, cut into chunks of sell_C rows, padded to the
+ * chunk's longest row with (column = own row, value 0) and stored column-major
+ * within each chunk.  also_single != 0 also stores R32/C64 values (round to
+ * nearest).  Synchronizes `stream`.  EINVAL on bad sizes, ENOMEM, ECUDA. */
+chebfd_status chebfd_matrix_create_csr(int64_t n, const int64_t* rowptr, const int32_t* col,
+                                       const void* val, chebfd_dtype val_dtype, int sell_C,
+                                       int sell_sigma, int also_single, void* stream,
+                                       chebfd_matrix** out);
+
+/* Generate a lattice Hamiltonian (see chebfd_lattice_desc) directly on the
+ * device and store it as SELL-C-sigma.  Synchronizes `stream`. */
+chebfd_status chebfd_matrix_create_lattice(const chebfd_lattice_desc* desc, void* stream,
+                                           chebfd_matrix** out);
+
+chebfd_status chebfd_matrix_get_info(const chebfd_matrix* H, chebfd_matrix_info* out);
+
+/* Copy the SELL arrays to HOST buffers sized from chebfd_matrix_get_info:
+ * chunk_ptr[nchunks+1] int64, chunk_len[nchunks] int32, col[nnz_padded] int32,
+ * val[nnz_padded] FP64 values (R64 or C128), perm[n] int64 (original row of
+ * sorted row r).  Any pointer may be NULL to skip that array.  Synchronous. */
+chebfd_status chebfd_matrix_export_sell(const chebfd_matrix* H, int64_t* chunk_ptr,
+                                        int32_t* chunk_len, int32_t* col, void* val,
+                                        int64_t* perm);
+
+chebfd_status chebfd_matrix_destroy(chebfd_matrix* H);
+
+/* ------------------------------------------------------------ kernels (K1) */
+
+/* Y = (alpha H + beta) X for a device block X (N x nb, ld), Y of the same
+ * shape (Y != X).  vdt selects the vector type and the matching value copy.
+ * Wider blocks than one kernel row group (C128/C64: 64, R64/R32: 128 columns)
+ * are processed as column panels.  Asynchronous on `stream`. */
+chebfd_status chebfd_spmv(const chebfd_matrix* H, double alpha, double beta, const void* X,
+                          void* Y, int64_t ld, int nb, chebfd_dtype vdt, void* stream);
+
+/* ------------------------------------------------ bounds and scaling (A1-A2) */
+
+/* Spectral interval [a, b] from `lanczos_steps` Lanczos steps (Sec. 3.1 step
+ * 1: 20-30 steps), FP64, full reorthogonalisation, start vector of SplitMix64
+ * stream 4 (entries 2u-1).  a = theta_min - rho_min, b = theta_max + rho_max
+ * (rho = Ritz residual bound |beta_m s_m,i|), widened by 1% of b-a on each side
+ * and clamped to the Gershgorin interval.  alpha = 2/(b-a), beta = (a+b)/(a-b)
+ * (Eq. W1).  All outputs are HOST scalars; any may be NULL.  Synchronizes. */
+chebfd_status chebfd_scale_bounds(const chebfd_matrix* H, int lanczos_steps, uint64_t seed,
+                                  double* a, double* b, double* alpha, double* beta,
+                                  void* stream);
+
+/* ------------------------------------------------------- coefficients (A3-A4) */
+
+/* gc[n] = g_n c_n, n = 0..Np, into a HOST array of Np+1 doubles: c_n are the
+ * Chebyshev coefficients of the rectangular window [lam_lo, lam_hi] inside
+ * [a, b] (Sec. 2.1, taken with the sign that makes p ~ +1 in the window:
+ * c_0 = (th_lo - th_hi)/pi, c_n = 2/(pi n)(sin n th_lo - sin n th_hi),
+ * th = arccos(alpha lam + beta) clamped), g_n the kernel factors of Tab. Kernel
+ * (mu is the Lanczos exponent, ignored otherwise).  Pure host math. */
+chebfd_status chebfd_window_coeffs(double a, double b, double lam_lo, double lam_hi, int Np,
+                                   chebfd_kernel kernel, double mu, double* gc);
+
+/* ---------------------------------------------------- filter (A5, K2, K4) */
+
+/* Replace the device block X (N x nb, row-major, ld) by p[H] X =
+ * sum_{n=0}^{Np} gc[n] T_n(alpha H + beta) X, following Fig. ChebFD: two start
+ * steps, then for n = 3..Np one fused kernel per step computing
+ * w <- 2(alpha H + beta) u - w and X <- X + gc[n] w in a single pass over the
+ * matrix and the vectors.  Np >= 2; gc is a HOST array of Np+1 doubles.
+ * If `moments` (DEVICE, 2*Np x nb doubles, row n = moment n) is non-NULL the
+ * same passes also produce the Chebyshev moments mu_n[k] = <x_k, T_n(A) x_k>
+ * of Sec. 4 (via mu_2n = 2<u_n,u_n> - mu_0, mu_2n+1 = 2<u_n+1,u_n> - mu_1),
+ * and the call synchronizes `stream` and returns ENUMERIC if a moment is NaN or
+ * |mu_2n| > 1.001 mu_0 + 1e-300 (|T_n| <= 1 only on [-1, 1]: spec(H) is not in
+ * [a, b]).  Work vectors are taken from the stream-ordered allocator.
+ * nb > one kernel row group is processed as column panels. */
+chebfd_status chebfd_filter_block(const chebfd_matrix* H, double alpha, double beta,
+                                  const double* gc, int Np, void* X, int64_t ld, int nb,
+                                  chebfd_dtype vdt, double* moments, void* stream);
+
+/* One fused Chebyshev step of Fig. ChebFD (the kernel that carries the filter,
+ * lines "w = 2(alpha H + beta) u - w ; x = x + g_n c_n w"): W <- 2(alpha H +
+ * beta) U - W and Y <- Y + c W in one pass, for device blocks U, W, Y of shape
+ * N x nb with a common leading dimension ld (U must not alias W or Y).  nb is
+ * limited to one row group (C128/C64: 64, R64/R32: 128 columns).
+ * Asynchronous on `stream`. */
+chebfd_status chebfd_chebyshev_step(const chebfd_matrix* H, double alpha, double beta, double c,
+                                    const void* U, void* W, void* Y, int64_t ld, int nb,
+                                    chebfd_dtype vdt, void* stream);
+
+/* -------------------------------------------------------------- KPM (A12) */
+
+/* Normalised KPM moments mu_n = Tr T_n(alpha H + beta) / N, n = 0..M-1, by
+ * stochastic trace over R probe vectors (Sec. 3.1 step 1, method of WWAF06):
+ * real entries +-1 (bit 0) or complex (+-1 +- i)/sqrt(2) (bits 0, 1) of the
+ * SplitMix64 word i*R + r of stream 2.  mu is a HOST array of M doubles, M
+ * even, M >= 2.  Synchronizes. */
+chebfd_status chebfd_kpm_moments(const chebfd_matrix* H, double alpha, double beta, int M,
+                                 int R, uint64_t seed, double* mu, void* stream);
+
+/* Random search block (Sec. 3.1 step 4): X[i*ld + k] = 2u - 1 (real) or
+ * (2u - 1) + i(2u' - 1) with u from SplitMix64 stream 1 at word index
+ * i*ns_total + (k + col0) (real) or 2*(i*ns_total + k + col0) + {0,1}.
+ * Columns col0 .. col0+nb-1 of an ns_total-wide search space. */
+chebfd_status chebfd_random_block(void* X, int64_t n, int64_t ld, int nb, int col0,
+                                  int ns_total, uint64_t seed, chebfd_dtype vdt, void* stream);
+
+/* ------------------------------------------- orthonormalisation (A7, K3, K5) */
+
+/* Rank-revealing SVQB (Sec. 3.1 step 6; Stathopoulos-Wu) of the device block Y
+ * (N x ns, row-major, ld, dtype R64 or C128), in place, all in FP64:
+ * S = Y^H Y (cuBLAS HERK/SYRK), D = diag(S)^-1/2, D S D = U Theta U^H
+ * (cuSOLVER), directions with Theta_i < ns 2^-52 max Theta dropped and
+ * replaced by fresh random vectors (SplitMix64 stream 3; the q-th refill
+ * column of the run uses word indices q*N + i, x2 for complex parts, with q
+ * continuing from *refill_counter), Y <- Y D U Theta^-1/2; repeated (at most 3
+ * passes) while refilled or while max|Y^H Y - I| > 1e-12.  rank (host, may be
+ * NULL) receives the rank found in the first pass.  ns <= 1024.  Synchronizes.
+ * ENUMERIC if the block has rank 0 or the eigensolver fails. */
+chebfd_status chebfd_orthonormalize(void* Y, int64_t n, int ns, int64_t ld, chebfd_dtype vdt,
+                                    uint64_t refill_seed, int64_t* refill_counter, int* rank,
+                                    void* stream);
+
+/* ---------------------------------------------- Rayleigh-Ritz (A8, K6, K7) */
+
+/* Rayleigh-Ritz step (Sec. 3.1 step 7) for an orthonormal FP64 device block Y
+ * (N x ns, ld): G = Y^H (H Y), symmetrised, eigenpairs (theta_k, s_k) in
+ * ascending order (cuSOLVER, FP64), Y <- Y S (the Ritz vectors, in place),
+ * residual norms res_k = ||H v_k - theta_k v_k|| formed as ||(HY) s_k -
+ * theta_k Y s_k|| without a further product with H.  theta[ns] and res[ns] are
+ * HOST arrays (res may be NULL); HV (device, N x ns, ld, may be NULL) receives
+ * H times the Ritz vectors.  Synchronizes. */
+chebfd_status chebfd_rayleigh_ritz(const chebfd_matrix* H, void* Y, int64_t ld, int ns,
+                                   chebfd_dtype vdt, double* theta, double* res, void* HV,
+                                   void* stream);
+
+/* res[k] = ||H v_k - theta_k v_k|| (FP64) for the k device vectors V (N x k,
+ * ld, R64/C128) and HOST theta[k]; res is a HOST array.  One product with H,
+ * per-column sums reduced in a fixed order.  Synchronizes. */
+chebfd_status chebfd_residuals(const chebfd_matrix* H, const void* V, const double* theta,
+                               int64_t ld, int k, chebfd_dtype vdt, double* res, void* stream);
+
+/* Y = X with a change of precision (R64 <-> R32, C128 <-> C64, or a copy);
+ * device blocks N x nb with leading dimensions ldx, ldy; round to nearest. */
+chebfd_status chebfd_convert_block(const void* X, chebfd_dtype xdt, int64_t ldx, void* Y,
+                                   chebfd_dtype ydt, int64_t ldy, int64_t n, int nb,
+                                   void* stream);
+
+/* ------------------------------------------------------------- solve (A10) */
+
+typedef enum chebfd_precision {
+    CHEBFD_PRECISION_FP64 = 0,  /* FP64 filter, FP64 orthonormalisation and Rayleigh-Ritz */
+    CHEBFD_PRECISION_MIXED = 1  /* FP32 / complex64 filter until the residuals stall, then
+                                   FP64 filter sweeps; FP64 orthonormalisation, RR, residuals */
+} chebfd_precision;
+
+/* Parameters of chebfd_solve.  Zero / negative fields take the defaults given. */
+typedef struct chebfd_params {
+    double lam_lo, lam_hi;   /* target interval I_T (closed) */
+    double eps;              /* converged if ||H v - theta v|| <= eps * ||H||, ||H|| = max(|a|,|b|) */
+    double a, b;             /* spectral interval; b <= a: computed by chebfd_scale_bounds */
+    double mu;               /* Lanczos kernel exponent (default 2) */
+    int32_t ns;              /* search space size N_S (required, <= 1024) */
+    int32_t Np;              /* filter degree N_p (required, >= 2) */
+    int32_t kernel;          /* chebfd_kernel (default LANCZOS) */
+    int32_t nb;              /* filter panel width (default 64 complex / 128 real) */
+    int32_t precision;       /* chebfd_precision */
+    int32_t max_iter;        /* default 50 */
+    int32_t lanczos_steps;   /* default 30 */
+    int32_t reserved;
+    uint64_t seed;           /* search-vector / refill / Lanczos seed */
+} chebfd_params;
+
+typedef struct chebfd_result chebfd_result;
+
+/* All eigenpairs of H in [lam_lo, lam_hi] by the ChebFD iteration of Sec. 3.1
+ * (steps 4-8): random search block (stream 1), then per iteration the filter
+ * p[H] of degree Np (chebfd_filter_block), SVQB (chebfd_orthonormalize),
+ * Rayleigh-Ritz (chebfd_rayleigh_ritz) and the convergence test.  Ghost Ritz
+ * pairs (Sec. 3.1 step 7): from the second iteration on, an in-window pair
+ * whose residual exceeds sqrt(eps) ||H|| and did not fall by >= 10x against
+ * the previous iteration's pair nearest in theta is discarded.  Converged
+ * when at least one pair is accepted and every accepted in-window pair has
+ * residual <= eps ||H||; the restart block is the set of Ritz vectors.
+ * MIXED precision switches to FP64 filter sweeps once the largest accepted
+ * residual exceeds 1e-9 ||H|| and fell by less than 2x in an iteration.
+ * Result handle owned by the library (chebfd_result_destroy).  ENOCONV when
+ * max_iter is reached (the result still holds the last iteration).
+ * Synchronizes. */
+chebfd_status chebfd_solve(const chebfd_matrix* H, const chebfd_params* p, void* stream,
+                           chebfd_result** out);
+
+/* Accepted pairs of a result: nev, lambda[nev] (host, ascending), V (device,
+ * N x nev row-major FP64: C128 for a complex H, R64 for a real one, ld = nev),
+ * res[nev] (host), and the iteration log. Pointers stay valid until destroy. */
+typedef struct chebfd_result_info {
+    int32_t nev;
+    int32_t iterations;
+    int32_t converged;
+    int32_t fp64_iterations;    /* iterations whose filter ran in FP64 */
+    int64_t n_mvm;              /* N_iter * N_S * N_p products with H (vector count) */
+    double a, b;                /* spectral interval used */
+    double seconds_filter, seconds_dense, seconds_total;
+    const double* lambda;
+    const double* res;
+    const void* V;
+} chebfd_result_info;
+
+chebfd_status chebfd_result_get(const chebfd_result* r, chebfd_result_info* out);
+
+/* Copy the accepted Ritz vectors (N x nev) into the caller's DEVICE buffer dst
+ * (row-major, leading dimension ld >= nev, same FP64 type as the result).
+ * Synchronizes `stream`. */
+chebfd_status chebfd_result_copy_vectors(const chebfd_result* r, void* dst, int64_t ld,
+                                         void* stream);
+
+chebfd_status chebfd_result_destroy(chebfd_result* r);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEBFD_H */

@@ -29,11 +29,19 @@ def probe_vectors(seed, D, R, complex_values):
 
 
 def moments(H, alpha, beta, M, R, seed, complex_values):
-    """mu_0..mu_{M-1}, the stochastic trace estimate of Tr T_n(A)/D."""
+    """mu_0..mu_{M-1}, the stochastic trace estimate of Tr T_n(A)/D; the
+    recurrence T_{n+1} = 2 A T_n - T_{n-1} is run once, keeping two vectors."""
     D = H.shape[0]
     r = probe_vectors(seed, D, R, complex_values)
-    mu = filt.moments(H, alpha, beta, r, M)          # M x R, per probe
-    return mu.sum(axis=1) / (R * D)
+    per = np.zeros((M, R))
+    t_prev, t_cur = None, r
+    for n in range(M):
+        per[n] = np.real(np.sum(np.conj(r) * t_cur, axis=0))
+        if n == 0:
+            t_prev, t_cur = t_cur, filt.apply_A(H, alpha, beta, r)
+        else:
+            t_prev, t_cur = t_cur, 2.0 * filt.apply_A(H, alpha, beta, t_cur) - t_prev
+    return per.sum(axis=1) / (R * D)
 
 
 def jackson_kpm(M):

@@ -98,9 +98,12 @@ def topi_csr(Lx, Ly, Lz, t=1.0, m=1.0, W=0.0, seed=0):
                 else:
                     cz = (z + sign) % Lz
                 sn = cx + Lx * (cy + Ly * cz)
-                # column site s+e_j carries T_j^dagger, column site s-e_j carries T_j
+                # column site s+e_j carries T_j^dagger, column site s-e_j carries T_j;
+                # off-diagonal entry q i h Gamma[o,p] (q = +1 for T_j, -1 for T_j^dagger)
+                # written out in real arithmetic, zeros as +0.0
                 dval = -h * g1[o]
-                off = (1j * h * G[o, p]) if sign < 0 else (-1j * h * G[o, p])
+                q = 1.0 if sign < 0 else -1.0
+                off = complex(-q * h * G[o, p].imag + 0.0, q * h * G[o, p].real + 0.0)
                 rows.append(r); cols.append(4 * sn + o)
                 vals.append(np.full(nsite, dval, dtype=np.complex128))
                 order.append(np.full(nsite, rank, dtype=np.int64)); rank += 1

@@ -1,0 +1,358 @@
+"""ctypes binding of libchebfd.so: argument marshalling only.
+
+The functions below carry the names of the C ABI (include/chebfd.h) and pass
+device pointers (torch tensors on the current CUDA device), host numpy arrays
+and the current torch stream through unchanged.  Every computation runs inside
+the library; if it is missing this module raises instead of falling back.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libchebfd.so")
+
+R64, C128, R32, C64 = 0, 1, 2, 3
+KERNEL_NONE, KERNEL_FEJER, KERNEL_JACKSON, KERNEL_LANCZOS = 0, 1, 2, 3
+LATTICE_TOPI, LATTICE_GRAPHENE = 0, 1
+KERNEL_IDS = {"none": KERNEL_NONE, "fejer": KERNEL_FEJER, "jackson": KERNEL_JACKSON,
+              "lanczos": KERNEL_LANCZOS}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "ENOCONV",
+          6: "ETIMEOUT", 7: "EUNSUPPORTED"}
+
+c_i64p = ctypes.POINTER(ctypes.c_int64)
+c_i32p = ctypes.POINTER(ctypes.c_int32)
+c_dp = ctypes.POINTER(ctypes.c_double)
+c_vp = ctypes.c_void_p
+
+
+class LatticeDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
+                ("Lz", ctypes.c_int32), ("t", ctypes.c_double), ("m", ctypes.c_double),
+                ("W", ctypes.c_double), ("seed", ctypes.c_uint64), ("sell_C", ctypes.c_int32),
+                ("sell_sigma", ctypes.c_int32), ("also_single", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class MatrixInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_padded", ctypes.c_int64),
+                ("nchunks", ctypes.c_int64), ("C", ctypes.c_int32), ("sigma", ctypes.c_int32),
+                ("max_row_len", ctypes.c_int32), ("is_complex", ctypes.c_int32),
+                ("has_single", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+# name -> (restype, argtypes); every function returns chebfd_status unless noted
+SIGNATURES = {
+    "chebfd_abi_version": (ctypes.c_int, []),
+    "chebfd_last_error": (ctypes.c_char_p, []),
+    "chebfd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "chebfd_matrix_create_csr": (ctypes.c_int, [ctypes.c_int64, c_i64p, c_i32p, c_vp, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_int, c_vp,
+                                                ctypes.POINTER(c_vp)]),
+    "chebfd_matrix_create_lattice": (ctypes.c_int, [ctypes.POINTER(LatticeDesc), c_vp,
+                                                    ctypes.POINTER(c_vp)]),
+    "chebfd_matrix_get_info": (ctypes.c_int, [c_vp, ctypes.POINTER(MatrixInfo)]),
+    "chebfd_matrix_export_sell": (ctypes.c_int, [c_vp, c_i64p, c_i32p, c_i32p, c_vp, c_i64p]),
+    "chebfd_matrix_destroy": (ctypes.c_int, [c_vp]),
+    "chebfd_spmv": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double, c_vp, c_vp,
+                                   ctypes.c_int64, ctypes.c_int, ctypes.c_int, c_vp]),
+    "chebfd_scale_bounds": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_uint64, c_dp, c_dp, c_dp,
+                                           c_dp, c_vp]),
+    "chebfd_window_coeffs": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, c_dp]),
+    "chebfd_filter_block": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double, c_dp,
+                                           ctypes.c_int, c_vp, ctypes.c_int64, ctypes.c_int,
+                                           ctypes.c_int, c_dp, c_vp]),
+    "chebfd_chebyshev_step": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, c_vp, c_vp, c_vp, ctypes.c_int64,
+                                             ctypes.c_int, ctypes.c_int, c_vp]),
+    "chebfd_kpm_moments": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_uint64, c_dp, c_vp]),
+    "chebfd_random_block": (ctypes.c_int, [c_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                           ctypes.c_int, c_vp]),
+    "chebfd_orthonormalize": (ctypes.c_int, [c_vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
+                                             ctypes.c_int, ctypes.c_uint64, c_i64p, c_i32p, c_vp]),
+    "chebfd_rayleigh_ritz": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int64, ctypes.c_int,
+                                            ctypes.c_int, c_dp, c_dp, c_vp, c_vp]),
+    "chebfd_residuals": (ctypes.c_int, [c_vp, c_vp, c_dp, ctypes.c_int64, ctypes.c_int,
+                                        ctypes.c_int, c_dp, c_vp]),
+    "chebfd_convert_block": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int64, c_vp,
+                                            ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                            ctypes.c_int, c_vp]),
+    "chebfd_solve": (ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.POINTER(c_vp)]),
+    "chebfd_result_get": (ctypes.c_int, [c_vp, c_vp]),
+    "chebfd_result_destroy": (ctypes.c_int, [c_vp]),
+    "chebfd_result_copy_vectors": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int64, c_vp]),
+}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("lam_lo", ctypes.c_double), ("lam_hi", ctypes.c_double), ("eps", ctypes.c_double),
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("mu", ctypes.c_double),
+                ("ns", ctypes.c_int32), ("Np", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("nb", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("lanczos_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class ResultInfo(ctypes.Structure):
+    _fields_ = [("nev", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("fp64_iterations", ctypes.c_int32),
+                ("n_mvm", ctypes.c_int64), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("seconds_filter", ctypes.c_double), ("seconds_dense", ctypes.c_double),
+                ("seconds_total", ctypes.c_double), ("lambda_", c_dp), ("res", c_dp),
+                ("V", c_vp)]
+
+
+class ChebFDError(RuntimeError):
+    def __init__(self, status, where, message):
+        super().__init__("%s: %s (%s)" % (where, STATUS.get(status, status), message))
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libchebfd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libchebfd.so not built: run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, where):
+    if status != 0:
+        msg = lib().chebfd_last_error()
+        raise ChebFDError(status, where, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    """Device or host pointer of a torch tensor / numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def dtype_of(t):
+    import torch
+    return {torch.float64: R64, torch.complex128: C128, torch.float32: R32,
+            torch.complex64: C64}[t.dtype]
+
+
+class Matrix:
+    """Owner of a chebfd_matrix handle (device SELL-C-sigma)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        info = MatrixInfo()
+        _check(lib().chebfd_matrix_get_info(handle, ctypes.byref(info)), "chebfd_matrix_get_info")
+        self.info = info
+
+    @property
+    def n(self):
+        return self.info.n
+
+    @property
+    def is_complex(self):
+        return bool(self.info.is_complex)
+
+    def close(self):
+        if self.handle:
+            _check(lib().chebfd_matrix_destroy(self.handle), "chebfd_matrix_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export_sell(self):
+        i = self.info
+        chunk_ptr = np.zeros(i.nchunks + 1, np.int64)
+        chunk_len = np.zeros(i.nchunks, np.int32)
+        col = np.zeros(i.nnz_padded, np.int32)
+        val = np.zeros(i.nnz_padded, np.complex128 if i.is_complex else np.float64)
+        perm = np.zeros(i.n, np.int64)
+        _check(lib().chebfd_matrix_export_sell(
+            self.handle, chunk_ptr.ctypes.data_as(c_i64p), chunk_len.ctypes.data_as(c_i32p),
+            col.ctypes.data_as(c_i32p), ctypes.c_void_p(val.ctypes.data),
+            perm.ctypes.data_as(c_i64p)), "chebfd_matrix_export_sell")
+        return dict(n=i.n, C=i.C, sigma=i.sigma, nchunks=i.nchunks, chunk_ptr=chunk_ptr,
+                    chunk_len=chunk_len, col=col, val=val, perm=perm)
+
+
+def chebfd_matrix_create_csr(rowptr, col, val, sell_C=1, sell_sigma=1, also_single=False,
+                             stream=None):
+    rowptr = np.ascontiguousarray(rowptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    cplx = np.iscomplexobj(val)
+    val = np.ascontiguousarray(val, np.complex128 if cplx else np.float64)
+    h = c_vp()
+    _check(lib().chebfd_matrix_create_csr(
+        len(rowptr) - 1, rowptr.ctypes.data_as(c_i64p), col.ctypes.data_as(c_i32p),
+        ctypes.c_void_p(val.ctypes.data), C128 if cplx else R64, sell_C, sell_sigma,
+        1 if also_single else 0, _stream(stream), ctypes.byref(h)), "chebfd_matrix_create_csr")
+    return Matrix(h)
+
+
+def chebfd_matrix_create_lattice(kind, Lx, Ly, Lz=1, t=1.0, m=1.0, W=0.0, seed=0, sell_C=1,
+                                 sell_sigma=1, also_single=False, stream=None):
+    d = LatticeDesc(kind=LATTICE_TOPI if kind in ("topi", LATTICE_TOPI) else LATTICE_GRAPHENE,
+                    Lx=Lx, Ly=Ly, Lz=Lz, t=t, m=m, W=W, seed=seed, sell_C=sell_C,
+                    sell_sigma=sell_sigma, also_single=1 if also_single else 0, reserved=0)
+    h = c_vp()
+    _check(lib().chebfd_matrix_create_lattice(ctypes.byref(d), _stream(stream), ctypes.byref(h)),
+           "chebfd_matrix_create_lattice")
+    return Matrix(h)
+
+
+def chebfd_spmv(H, alpha, beta, X, Y, stream=None):
+    n, nb = X.shape[0], X.shape[1]
+    ld = X.stride(0)
+    assert Y.stride(0) == ld and X.dtype == Y.dtype
+    _check(lib().chebfd_spmv(H.handle, alpha, beta, _ptr(X), _ptr(Y), ld, nb, dtype_of(X),
+                             _stream(stream)), "chebfd_spmv")
+
+
+def chebfd_scale_bounds(H, lanczos_steps=30, seed=0, stream=None):
+    a, b, al, be = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().chebfd_scale_bounds(H.handle, lanczos_steps, seed, ctypes.byref(a),
+                                     ctypes.byref(b), ctypes.byref(al), ctypes.byref(be),
+                                     _stream(stream)), "chebfd_scale_bounds")
+    return a.value, b.value, al.value, be.value
+
+
+def chebfd_window_coeffs(a, b, lam_lo, lam_hi, Np, kernel="lanczos", mu=2.0):
+    gc = np.zeros(Np + 1)
+    k = KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel)
+    _check(lib().chebfd_window_coeffs(a, b, lam_lo, lam_hi, Np, k, mu, gc.ctypes.data_as(c_dp)),
+           "chebfd_window_coeffs")
+    return gc
+
+
+def chebfd_filter_block(H, alpha, beta, gc, X, moments=None, stream=None):
+    """In place: X <- p[H] X for a device tensor X (N x nb, row stride ld)."""
+    gc = np.ascontiguousarray(gc, np.float64)
+    Np = len(gc) - 1
+    n, nb = X.shape[0], X.shape[1]
+    mp = ctypes.cast(ctypes.c_void_p(moments.data_ptr()), c_dp) if moments is not None else None
+    _check(lib().chebfd_filter_block(H.handle, alpha, beta, gc.ctypes.data_as(c_dp), Np, _ptr(X),
+                                     X.stride(0), nb, dtype_of(X), mp, _stream(stream)),
+           "chebfd_filter_block")
+
+
+def chebfd_chebyshev_step(H, alpha, beta, c, U, W, Y, stream=None):
+    """W <- 2(alpha H + beta) U - W ; Y <- Y + c W (one fused step)."""
+    n, nb = U.shape[0], U.shape[1]
+    ld = U.stride(0)
+    assert W.stride(0) == ld and Y.stride(0) == ld
+    _check(lib().chebfd_chebyshev_step(H.handle, alpha, beta, c, _ptr(U), _ptr(W), _ptr(Y), ld, nb,
+                                       dtype_of(U), _stream(stream)), "chebfd_chebyshev_step")
+
+
+def chebfd_kpm_moments(H, alpha, beta, M, R, seed=0, stream=None):
+    mu = np.zeros(M)
+    _check(lib().chebfd_kpm_moments(H.handle, alpha, beta, M, R, seed, mu.ctypes.data_as(c_dp),
+                                    _stream(stream)), "chebfd_kpm_moments")
+    return mu
+
+
+def chebfd_orthonormalize(Y, seed=0, refill_counter=0, stream=None):
+    """In place SVQB of a device FP64 block; returns (rank, new refill counter)."""
+    n, ns = Y.shape[0], Y.shape[1]
+    cnt = ctypes.c_int64(refill_counter)
+    rank = ctypes.c_int32(0)
+    _check(lib().chebfd_orthonormalize(_ptr(Y), n, ns, Y.stride(0), dtype_of(Y), seed,
+                                       ctypes.byref(cnt), ctypes.byref(rank), _stream(stream)),
+           "chebfd_orthonormalize")
+    return rank.value, cnt.value
+
+
+def chebfd_rayleigh_ritz(H, Y, HV=None, stream=None):
+    """In place: Y <- Ritz vectors; returns (theta, residuals) as numpy arrays."""
+    ns = Y.shape[1]
+    theta = np.zeros(ns)
+    res = np.zeros(ns)
+    _check(lib().chebfd_rayleigh_ritz(H.handle, _ptr(Y), Y.stride(0), ns, dtype_of(Y),
+                                      theta.ctypes.data_as(c_dp), res.ctypes.data_as(c_dp),
+                                      _ptr(HV), _stream(stream)), "chebfd_rayleigh_ritz")
+    return theta, res
+
+
+def chebfd_residuals(H, V, theta, stream=None):
+    k = V.shape[1]
+    theta = np.ascontiguousarray(theta, np.float64)
+    res = np.zeros(k)
+    _check(lib().chebfd_residuals(H.handle, _ptr(V), theta.ctypes.data_as(c_dp), V.stride(0), k,
+                                  dtype_of(V), res.ctypes.data_as(c_dp), _stream(stream)),
+           "chebfd_residuals")
+    return res
+
+
+def chebfd_convert_block(X, Y, stream=None):
+    """Y <- X with a change of precision (device blocks of equal shape)."""
+    _check(lib().chebfd_convert_block(_ptr(X), dtype_of(X), X.stride(0), _ptr(Y), dtype_of(Y),
+                                      Y.stride(0), X.shape[0], X.shape[1], _stream(stream)),
+           "chebfd_convert_block")
+
+
+def chebfd_solve(H, lam_lo, lam_hi, ns, Np, eps=1e-9, kernel="lanczos", mu=2.0, nb=0,
+                 precision="fp64", max_iter=50, seed=0, a=0.0, b=0.0, lanczos_steps=30,
+                 stream=None):
+    """Run ChebFD; returns a dict with lambda, res (numpy), V (torch, device) and the log."""
+    import torch
+    p = Params(lam_lo=lam_lo, lam_hi=lam_hi, eps=eps, a=a, b=b, mu=mu, ns=ns, Np=Np,
+               kernel=KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel), nb=nb,
+               precision=1 if precision == "mixed" else 0, max_iter=max_iter,
+               lanczos_steps=lanczos_steps, reserved=0, seed=seed)
+    h = c_vp()
+    st = lib().chebfd_solve(H.handle, ctypes.byref(p), _stream(stream), ctypes.byref(h))
+    if st not in (0, 5) or not h:
+        _check(st, "chebfd_solve")
+    info = ResultInfo()
+    try:
+        _check(lib().chebfd_result_get(h, ctypes.byref(info)), "chebfd_result_get")
+        nev = info.nev
+        lam = np.ctypeslib.as_array(info.lambda_, (nev,)).copy() if nev else np.zeros(0)
+        res = np.ctypeslib.as_array(info.res, (nev,)).copy() if nev else np.zeros(0)
+        dt = torch.complex128 if H.is_complex else torch.float64
+        V = torch.empty((H.n, max(nev, 1)), dtype=dt, device="cuda")[:, :nev]
+        if nev:
+            _check(lib().chebfd_result_copy_vectors(h, _ptr(V), V.stride(0), _stream(stream)),
+                   "chebfd_result_copy_vectors")
+        out = dict(lam=lam, res=res, V=V, nev=nev, iterations=info.iterations,
+                   converged=bool(info.converged), fp64_iterations=info.fp64_iterations,
+                   n_mvm=info.n_mvm, a=info.a, b=info.b, seconds_filter=info.seconds_filter,
+                   seconds_dense=info.seconds_dense, seconds_total=info.seconds_total,
+                   status=STATUS[st])
+    finally:
+        lib().chebfd_result_destroy(h)
+    return out
+
+
+def chebfd_random_block(X, col0=0, ns_total=None, seed=0, stream=None):
+    n, nb = X.shape[0], X.shape[1]
+    ns_total = nb if ns_total is None else ns_total
+    _check(lib().chebfd_random_block(_ptr(X), n, X.stride(0), nb, col0, ns_total, seed,
+                                     dtype_of(X), _stream(stream)), "chebfd_random_block")

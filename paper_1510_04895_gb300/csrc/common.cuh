@@ -1,0 +1,159 @@
+// Internal declarations shared by the translation units of libchebfd.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/chebfd.h"
+
+namespace chebfd {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const std::string& msg);
+
+struct Error {
+    chebfd_status code;
+    std::string msg;
+};
+
+#define CHEBFD_CHECK_CUDA(expr)                                                       \
+    do {                                                                              \
+        cudaError_t e_ = (expr);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            throw ::chebfd::Error{e_ == cudaErrorMemoryAllocation ? CHEBFD_ENOMEM     \
+                                                                   : CHEBFD_ECUDA,    \
+                                  std::string(#expr) + ": " + cudaGetErrorString(e_)}; \
+        }                                                                             \
+    } while (0)
+
+#define CHEBFD_REQUIRE(cond, code, msg)                               \
+    do {                                                              \
+        if (!(cond)) throw ::chebfd::Error{(code), std::string(msg)}; \
+    } while (0)
+
+// Run `body` and translate exceptions into a status + thread-local message.
+template <class F>
+chebfd_status guarded(F&& body) {
+    try {
+        body();
+        return CHEBFD_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return CHEBFD_ENOMEM;
+    } catch (const std::exception& e) {
+        set_error(e.what());
+        return CHEBFD_ECUDA;
+    }
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool is_complex(chebfd_dtype d) { return d == CHEBFD_C128 || d == CHEBFD_C64; }
+inline bool is_single(chebfd_dtype d) { return d == CHEBFD_R32 || d == CHEBFD_C64; }
+inline size_t dtype_size(chebfd_dtype d) {
+    switch (d) {
+        case CHEBFD_R64: return 8;
+        case CHEBFD_C128: return 16;
+        case CHEBFD_R32: return 4;
+        case CHEBFD_C64: return 8;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------- matrix
+
+// Device SELL-C-sigma storage (column-major inside chunks of C rows).
+struct Matrix {
+    int64_t n = 0;
+    int64_t nnz = 0;
+    int64_t nnz_padded = 0;
+    int64_t nchunks = 0;
+    int C = 1, sigma = 1;
+    int max_row_len = 0;
+    bool complex_values = false;
+    bool identity_perm = true;
+    int64_t* chunk_ptr = nullptr;  // [nchunks+1]
+    int32_t* chunk_len = nullptr;  // [nchunks]
+    int32_t* col = nullptr;        // [nnz_padded]
+    int64_t* perm = nullptr;       // [n], original row of sorted row r
+    void* val64 = nullptr;         // double or double2 [nnz_padded]
+    void* val32 = nullptr;         // float or float2 [nnz_padded], optional
+    // Row panel order used by the kernels (same as sorted order here).
+    int device = 0;
+    int num_sms = 0;
+};
+
+// Build the SELL arrays from a device CSR (rowptr[n+1], col, FP64 values).
+// Takes ownership of nothing; the CSR buffers may be freed afterwards.
+void build_sell_from_device_csr(Matrix& M, const int64_t* d_rowptr, const int32_t* d_col,
+                                const void* d_val, int C, int sigma, bool also_single,
+                                cudaStream_t stream);
+
+void generate_lattice_csr(const chebfd_lattice_desc& d, int64_t* n_out, int64_t** d_rowptr,
+                          int32_t** d_col, void** d_val, cudaStream_t stream);
+
+// ---------------------------------------------------------------- kernels
+
+enum StepMode { MODE_SPMV = 0, MODE_SECOND = 1, MODE_STEP = 2 };
+
+struct StepArgs {
+    // Vectors (row-major, ld elements per row).
+    const void* gather;  // u: gathered through H (input of the product)
+    void* w;             // MODE_SPMV: output; MODE_SECOND: output w; MODE_STEP: in/out w
+    void* y;             // MODE_SECOND/STEP: accumulated block (in/out); unused for SPMV
+    int64_t ldg, ldw, ldy;  // leading dimensions (elements) of gather, w, y
+    int nb;
+    double alpha, beta;  // A = alpha H + beta
+    double c0, c1, c2;   // MODE_SECOND: y = c0 x + c1 u + c2 w ; MODE_STEP: y += c0 w
+    // Moments (optional): device partial buffer and output.
+    double* partials;    // [grid * 2 * nb]
+    unsigned int* counter;
+    double* moments;     // [2*Np x mom_ld]; nullptr = no dots
+    int64_t mom_ld;
+    int mom_step;        // n of the step: writes mu_{2n-2}, mu_{2n-1} (SPMV: mu_0, mu_1)
+};
+
+// Launch one step kernel.  dt selects the vector type, `single` the matrix copy.
+void launch_step(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs& a,
+                 cudaStream_t stream);
+int step_grid_size(const Matrix& M, chebfd_dtype dt, int nb);
+int max_panel_width(chebfd_dtype dt);
+
+void launch_random_block(void* X, int64_t n, int64_t ld, int nb, int col0, int ns_total,
+                         uint64_t seed, chebfd_dtype dt, cudaStream_t stream);
+void launch_kpm_probes(void* X, int64_t n, int64_t ld, int R, uint64_t seed, chebfd_dtype dt,
+                       cudaStream_t stream);
+
+// Device SplitMix64: i-th output of the generator started at seed*256 + stream.
+__host__ __device__ inline uint64_t splitmix_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__host__ __device__ inline uint64_t splitmix_word(uint64_t seed, uint64_t stream,
+                                                  uint64_t index) {
+    uint64_t state = seed * 256ULL + stream;
+    return splitmix_mix(state + (index + 1ULL) * 0x9E3779B97F4A7C15ULL);
+}
+__host__ __device__ inline double splitmix_uniform(uint64_t seed, uint64_t stream,
+                                                   uint64_t index) {
+    return (double)(splitmix_word(seed, stream, index) >> 11) * 0x1.0p-53;
+}
+
+constexpr uint64_t STREAM_DISORDER = 0;
+constexpr uint64_t STREAM_SEARCH = 1;
+constexpr uint64_t STREAM_KPM = 2;
+constexpr uint64_t STREAM_REFILL = 3;
+constexpr uint64_t STREAM_LANCZOS = 4;
+
+}  // namespace chebfd
+
+struct chebfd_matrix {
+    chebfd::Matrix m;
+};

@@ -1,0 +1,355 @@
+// Host side of the filter path: step dispatch, the filter of Fig. ChebFD, the
+// plain product Y = (alpha H + beta) X, KPM moments and random blocks.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "filter_kernels.cuh"
+
+namespace chebfd {
+
+void launch_step_f64(const SellView& H, bool cplx, StepMode mode, const StepArgs& a, int wc,
+                     int grid, cudaStream_t s);
+void launch_step_f32(const SellView& H, bool cplx, StepMode mode, const StepArgs& a, int wc,
+                     int grid, cudaStream_t s);
+
+namespace {
+
+int env_int(const char* name, int dflt) {
+    const char* v = getenv(name);
+    return v ? atoi(v) : dflt;
+}
+
+SellView view_of(const Matrix& M, bool single) {
+    SellView v;
+    v.chunk_ptr = M.chunk_ptr;
+    v.chunk_len = M.chunk_len;
+    v.col = M.col;
+    v.val = single ? M.val32 : M.val64;
+    v.perm = M.identity_perm ? nullptr : M.perm;
+    v.n = M.n;
+    v.C = M.C;
+    return v;
+}
+
+// 16-byte chunks per row of an nb-wide block.
+int chunks_per_row(chebfd_dtype dt, int nb) { return (int)((size_t)nb * dtype_size(dt) / 16); }
+
+}  // namespace
+
+int max_panel_width(chebfd_dtype dt) {
+    // 64 chunks of 16 bytes per row group: 64 complex doubles, 128 complex floats,
+    // 128 doubles, 256 floats; kept at 64 / 128 to bound register use.
+    switch (dt) {
+        case CHEBFD_C128: return 64;
+        case CHEBFD_C64: return 64;
+        case CHEBFD_R64: return 128;
+        case CHEBFD_R32: return 128;
+    }
+    return 0;
+}
+
+int step_grid_size(const Matrix& M, chebfd_dtype, int) {
+    // Persistent grid: whole waves of resident blocks on every SM.  The block
+    // count per SM is bounded by 2048 threads / 256 and by the CHEBFD_STEP_BPS
+    // override used by the autotuner.
+    int bps = env_int("CHEBFD_STEP_BPS", 4);
+    if (bps < 1) bps = 1;
+    if (bps > 8) bps = 8;
+    return M.num_sms * bps;
+}
+
+void validate_block(const Matrix& M, chebfd_dtype dt, const void* X, int64_t ld, int nb) {
+    CHEBFD_REQUIRE(X != nullptr, CHEBFD_EINVAL, "null block pointer");
+    CHEBFD_REQUIRE(nb >= 1 && ld >= nb, CHEBFD_EINVAL, "need 1 <= nb <= ld");
+    CHEBFD_REQUIRE(is_complex(dt) == M.complex_values, CHEBFD_EINVAL,
+                   "vector dtype must match the matrix (complex vs real)");
+    CHEBFD_REQUIRE(!is_single(dt) || M.val32 != nullptr, CHEBFD_EINVAL,
+                   "single-precision vectors need a matrix built with also_single");
+    CHEBFD_REQUIRE(((uintptr_t)X % 16) == 0, CHEBFD_EINVAL, "block base must be 16-byte aligned");
+    CHEBFD_REQUIRE(((size_t)ld * dtype_size(dt)) % 16 == 0, CHEBFD_EINVAL,
+                   "ld * element size must be a multiple of 16 bytes");
+    CHEBFD_REQUIRE(((size_t)nb * dtype_size(dt)) % 16 == 0, CHEBFD_EINVAL,
+                   "nb * element size must be a multiple of 16 bytes");
+}
+
+void launch_step(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs& a,
+                 cudaStream_t stream) {
+    const int wc = chunks_per_row(dt, a.nb);
+    CHEBFD_REQUIRE(wc >= 1 && wc <= 64, CHEBFD_EINVAL, "panel too wide for one row group");
+    const SellView v = view_of(M, is_single(dt));
+    const int grid = step_grid_size(M, dt, a.nb);
+    if (is_single(dt))
+        launch_step_f32(v, is_complex(dt), mode, a, wc, grid, stream);
+    else
+        launch_step_f64(v, is_complex(dt), mode, a, wc, grid, stream);
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ random blocks
+
+namespace {
+
+template <class R, bool CPLX>
+__global__ void random_block_kernel(R* X, int64_t n, int64_t ld, int nb, int col0, int ns_total,
+                                    uint64_t seed) {
+    const int64_t total = n * nb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / nb;
+        const int k = (int)(t - i * nb);
+        const uint64_t idx = (uint64_t)i * (uint64_t)ns_total + (uint64_t)(k + col0);
+        if (CPLX) {
+            const double re = 2.0 * splitmix_uniform(seed, STREAM_SEARCH, 2 * idx) - 1.0;
+            const double im = 2.0 * splitmix_uniform(seed, STREAM_SEARCH, 2 * idx + 1) - 1.0;
+            X[2 * (i * ld + k)] = (R)re;
+            X[2 * (i * ld + k) + 1] = (R)im;
+        } else {
+            X[i * ld + k] = (R)(2.0 * splitmix_uniform(seed, STREAM_SEARCH, idx) - 1.0);
+        }
+    }
+}
+
+template <class R, bool CPLX>
+__global__ void kpm_probe_kernel(R* X, int64_t n, int64_t ld, int R_, uint64_t seed) {
+    const int64_t total = n * R_;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / R_;
+        const int r = (int)(t - i * R_);
+        const uint64_t w = splitmix_word(seed, STREAM_KPM, (uint64_t)t);
+        const double s0 = (w & 1ULL) ? -1.0 : 1.0;
+        if (CPLX) {
+            const double s1 = (w & 2ULL) ? -1.0 : 1.0;
+            const double h = 0.70710678118654752440;  // 1/sqrt(2), correctly rounded
+            X[2 * (i * ld + r)] = (R)(s0 * h);
+            X[2 * (i * ld + r) + 1] = (R)(s1 * h);
+        } else {
+            X[i * ld + r] = (R)s0;
+        }
+    }
+}
+
+int small_grid(int64_t work) {
+    int64_t g = (work + 255) / 256;
+    return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 4096);
+}
+
+}  // namespace
+
+void launch_random_block(void* X, int64_t n, int64_t ld, int nb, int col0, int ns_total,
+                         uint64_t seed, chebfd_dtype dt, cudaStream_t s) {
+    const int g = small_grid(n * nb);
+    switch (dt) {
+        case CHEBFD_R64:
+            random_block_kernel<double, false><<<g, 256, 0, s>>>((double*)X, n, ld, nb, col0, ns_total, seed);
+            break;
+        case CHEBFD_C128:
+            random_block_kernel<double, true><<<g, 256, 0, s>>>((double*)X, n, ld, nb, col0, ns_total, seed);
+            break;
+        case CHEBFD_R32:
+            random_block_kernel<float, false><<<g, 256, 0, s>>>((float*)X, n, ld, nb, col0, ns_total, seed);
+            break;
+        case CHEBFD_C64:
+            random_block_kernel<float, true><<<g, 256, 0, s>>>((float*)X, n, ld, nb, col0, ns_total, seed);
+            break;
+    }
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+}
+
+void launch_kpm_probes(void* X, int64_t n, int64_t ld, int R, uint64_t seed, chebfd_dtype dt,
+                       cudaStream_t s) {
+    const int g = small_grid(n * R);
+    switch (dt) {
+        case CHEBFD_R64: kpm_probe_kernel<double, false><<<g, 256, 0, s>>>((double*)X, n, ld, R, seed); break;
+        case CHEBFD_C128: kpm_probe_kernel<double, true><<<g, 256, 0, s>>>((double*)X, n, ld, R, seed); break;
+        case CHEBFD_R32: kpm_probe_kernel<float, false><<<g, 256, 0, s>>>((float*)X, n, ld, R, seed); break;
+        case CHEBFD_C64: kpm_probe_kernel<float, true><<<g, 256, 0, s>>>((float*)X, n, ld, R, seed); break;
+    }
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ workspace
+
+namespace {
+
+struct DeviceBuffer {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    DeviceBuffer(size_t bytes, cudaStream_t stream) : s(stream) {
+        if (bytes) CHEBFD_CHECK_CUDA(cudaMallocAsync(&p, bytes, stream));
+    }
+    ~DeviceBuffer() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    DeviceBuffer(const DeviceBuffer&) = delete;
+    DeviceBuffer& operator=(const DeviceBuffer&) = delete;
+};
+
+int64_t padded_ld(chebfd_dtype dt, int nb) {
+    const size_t per = 16 / std::min<size_t>(16, dtype_size(dt));
+    return ((nb + (int64_t)per - 1) / (int64_t)per) * (int64_t)per;
+}
+
+// One panel of the filter of Fig. ChebFD; U, W: workspace panels (ldw).
+void filter_panel(const Matrix& M, double alpha, double beta, const double* gc, int Np, char* X,
+                  int64_t ld, int nb, chebfd_dtype dt, double* moments, int64_t mom_ld,
+                  char* U, char* W, int64_t ldw, double* partials, unsigned int* counter,
+                  cudaStream_t s) {
+    StepArgs a{};
+    a.nb = nb;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.partials = partials;
+    a.counter = counter;
+    a.moments = moments;
+    a.mom_ld = mom_ld;
+    // Step 1: u = A x
+    a.gather = X;
+    a.ldg = ld;
+    a.w = U;
+    a.ldw = ldw;
+    a.y = nullptr;
+    a.ldy = 0;
+    a.mom_step = 1;
+    launch_step(M, dt, MODE_SPMV, a, s);
+    // Step 2: w = 2 A u - x ; x = g0c0 x + g1c1 u + g2c2 w
+    a.gather = U;
+    a.ldg = ldw;
+    a.w = W;
+    a.ldw = ldw;
+    a.y = X;
+    a.ldy = ld;
+    a.c0 = gc[0];
+    a.c1 = gc[1];
+    a.c2 = gc[2];
+    a.mom_step = 2;
+    launch_step(M, dt, MODE_SECOND, a, s);
+    // Steps n = 3..Np: swap(w, u); w = 2 A u - w; x = x + gn cn w
+    char* u = U;
+    char* w = W;
+    for (int n = 3; n <= Np; ++n) {
+        std::swap(u, w);
+        a.gather = u;
+        a.w = w;
+        a.c0 = gc[n];
+        a.mom_step = n;
+        launch_step(M, dt, MODE_STEP, a, s);
+    }
+}
+
+}  // namespace
+
+void filter_block_impl(const Matrix& M, double alpha, double beta, const double* gc, int Np,
+                       void* X, int64_t ld, int nb, chebfd_dtype dt, double* moments,
+                       cudaStream_t s, int panel) {
+    validate_block(M, dt, X, ld, nb);
+    CHEBFD_REQUIRE(gc != nullptr && Np >= 2, CHEBFD_EINVAL, "need Np >= 2 and coefficients");
+    CHEBFD_REQUIRE(std::isfinite(alpha) && std::isfinite(beta), CHEBFD_EINVAL,
+                   "alpha, beta must be finite");
+    const int pw = panel > 0 ? std::min(panel, max_panel_width(dt)) : max_panel_width(dt);
+    const int wmax = std::min(pw, nb);
+    const int64_t ldw = padded_ld(dt, wmax);
+    const size_t es = dtype_size(dt);
+    DeviceBuffer U((size_t)M.n * ldw * es, s), W((size_t)M.n * ldw * es, s);
+    const int grid_max = M.num_sms * 8;
+    DeviceBuffer part(moments ? (size_t)grid_max * 2 * wmax * sizeof(double) : 0, s);
+    DeviceBuffer cnt(moments ? 256 : 0, s);
+    if (moments) CHEBFD_CHECK_CUDA(cudaMemsetAsync(cnt.p, 0, 256, s));
+    for (int p0 = 0; p0 < nb; p0 += pw) {
+        const int pnb = std::min(pw, nb - p0);
+        CHEBFD_REQUIRE(((size_t)pnb * es) % 16 == 0, CHEBFD_EINVAL,
+                       "panel width * element size must be a multiple of 16 bytes");
+        filter_panel(M, alpha, beta, gc, Np, (char*)X + p0 * es, ld, pnb, dt,
+                     moments ? moments + p0 : nullptr, nb, (char*)U.p, (char*)W.p, ldw,
+                     (double*)part.p, (unsigned int*)cnt.p, s);
+    }
+    if (moments) {
+        std::vector<double> h((size_t)2 * Np * nb);
+        CHEBFD_CHECK_CUDA(cudaMemcpyAsync(h.data(), moments, h.size() * sizeof(double),
+                                          cudaMemcpyDeviceToHost, s));
+        CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+        for (int k = 0; k < nb; ++k) {
+            const double mu0 = h[k];
+            for (int n = 0; n < 2 * Np; ++n) {
+                const double v = h[(size_t)n * nb + k];
+                CHEBFD_REQUIRE(std::isfinite(v), CHEBFD_ENUMERIC, "NaN/Inf Chebyshev moment");
+                if (n % 2 == 0)
+                    CHEBFD_REQUIRE(std::fabs(v) <= 1.001 * mu0 + 1e-300, CHEBFD_ENUMERIC,
+                                   "Chebyshev recurrence diverged: spectrum not inside [a,b]");
+            }
+        }
+    }
+}
+
+void spmv_impl(const Matrix& M, double alpha, double beta, const void* X, void* Y, int64_t ld,
+               int nb, chebfd_dtype dt, cudaStream_t s) {
+    validate_block(M, dt, X, ld, nb);
+    validate_block(M, dt, Y, ld, nb);
+    CHEBFD_REQUIRE(X != Y, CHEBFD_EINVAL, "spmv needs Y != X");
+    const int pw = max_panel_width(dt);
+    const size_t es = dtype_size(dt);
+    for (int p0 = 0; p0 < nb; p0 += pw) {
+        StepArgs a{};
+        a.nb = std::min(pw, nb - p0);
+        a.alpha = alpha;
+        a.beta = beta;
+        a.gather = (const char*)X + p0 * es;
+        a.ldg = ld;
+        a.w = (char*)Y + p0 * es;
+        a.ldw = ld;
+        launch_step(M, dt, MODE_SPMV, a, s);
+    }
+}
+
+void chebyshev_step_impl(const Matrix& M, double alpha, double beta, double c, const void* U,
+                         void* W, void* Y, int64_t ld, int nb, chebfd_dtype dt, cudaStream_t s) {
+    validate_block(M, dt, U, ld, nb);
+    validate_block(M, dt, W, ld, nb);
+    validate_block(M, dt, Y, ld, nb);
+    CHEBFD_REQUIRE(U != W && U != Y && W != Y, CHEBFD_EINVAL, "U, W, Y must be distinct");
+    CHEBFD_REQUIRE(nb <= max_panel_width(dt), CHEBFD_EINVAL, "nb wider than one row group");
+    StepArgs a{};
+    a.nb = nb;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.c0 = c;
+    a.gather = U;
+    a.ldg = ld;
+    a.w = W;
+    a.ldw = ld;
+    a.y = Y;
+    a.ldy = ld;
+    launch_step(M, dt, MODE_STEP, a, s);
+}
+
+void kpm_impl(const Matrix& M, double alpha, double beta, int Mm, int R, uint64_t seed,
+              double* mu, cudaStream_t s) {
+    CHEBFD_REQUIRE(Mm >= 2 && Mm % 2 == 0, CHEBFD_EINVAL, "M must be even and >= 2");
+    CHEBFD_REQUIRE(R >= 1, CHEBFD_EINVAL, "need R >= 1 probe vectors");
+    CHEBFD_REQUIRE(mu != nullptr, CHEBFD_EINVAL, "null output");
+    const chebfd_dtype dt = M.complex_values ? CHEBFD_C128 : CHEBFD_R64;
+    const int Np = Mm / 2;
+    // Probes go through the filter with gc = 0 (only the moments are kept).
+    const int64_t ld = padded_ld(dt, R);
+    const size_t es = dtype_size(dt);
+    DeviceBuffer X((size_t)M.n * ld * es, s);
+    CHEBFD_CHECK_CUDA(cudaMemsetAsync(X.p, 0, (size_t)M.n * ld * es, s));
+    launch_kpm_probes(X.p, M.n, ld, R, seed, dt, s);
+    DeviceBuffer mom((size_t)2 * std::max(Np, 2) * ld * sizeof(double), s);
+    std::vector<double> gc(std::max(Np, 2) + 1, 0.0);
+    // The padded columns are zero vectors: their moments are 0 and are ignored.
+    filter_block_impl(M, alpha, beta, gc.data(), std::max(Np, 2), X.p, ld, (int)ld, dt,
+                      (double*)mom.p, s, 0);
+    std::vector<double> h((size_t)2 * std::max(Np, 2) * ld);
+    CHEBFD_CHECK_CUDA(cudaMemcpyAsync(h.data(), mom.p, h.size() * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+    CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    for (int n = 0; n < Mm; ++n) {
+        double acc = 0.0;
+        for (int r = 0; r < R; ++r) acc += h[(size_t)n * ld + r];
+        mu[n] = acc / ((double)R * (double)M.n);
+    }
+}
+
+}  // namespace chebfd

@@ -1,0 +1,289 @@
+// The ChebFD iteration (Sec. 3.1, steps 4-8) orchestrated on the host around
+// the device kernels: filter, SVQB, Rayleigh-Ritz, convergence and ghost test.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace chebfd {
+
+void filter_block_impl(const Matrix& M, double alpha, double beta, const double* gc, int Np,
+                       void* X, int64_t ld, int nb, chebfd_dtype dt, double* moments,
+                       cudaStream_t s, int panel = 0);
+void scale_bounds_impl(const Matrix& M, int steps, uint64_t seed, double* a_out, double* b_out,
+                       cudaStream_t s);
+void orthonormalize_impl(void* Yv, int64_t n, int ns, int64_t ld, chebfd_dtype dt,
+                         uint64_t seed, int64_t* refill_counter, int* rank_out, cudaStream_t s);
+void rayleigh_ritz_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype dt,
+                        double* theta_host, double* res_host, void* HY_out, cudaStream_t s);
+void convert_block_impl(const void* X, chebfd_dtype xdt, int64_t ldx, void* Y, chebfd_dtype ydt,
+                        int64_t ldy, int64_t n, int nb, cudaStream_t s);
+void launch_random_block(void* X, int64_t n, int64_t ld, int nb, int col0, int ns_total,
+                         uint64_t seed, chebfd_dtype dt, cudaStream_t stream);
+int max_panel_width(chebfd_dtype dt);
+
+}  // namespace chebfd
+
+struct chebfd_result {
+    chebfd_result_info info{};
+    std::vector<double> lambda, res;
+    void* V = nullptr;
+    int64_t n = 0;
+    size_t elem_size = 0;
+};
+
+namespace chebfd {
+
+namespace {
+
+// gc[n] = g_n c_n (Sec. 2.1, Tab. Kernel) - the same construction as the
+// chebfd_window_coeffs entry point.
+std::vector<double> coefficients(double a, double b, double lo, double hi, int Np, int kernel,
+                                 double mu) {
+    std::vector<double> gc(Np + 1);
+    const chebfd_status st =
+        chebfd_window_coeffs(a, b, lo, hi, Np, (chebfd_kernel)kernel, mu, gc.data());
+    CHEBFD_REQUIRE(st == CHEBFD_OK, st, "coefficient construction failed");
+    return gc;
+}
+
+struct DevMem {
+    void* p = nullptr;
+    explicit DevMem(size_t bytes) {
+        if (bytes) CHEBFD_CHECK_CUDA(cudaMalloc(&p, bytes));
+    }
+    ~DevMem() { cudaFree(p); }
+    DevMem(const DevMem&) = delete;
+    DevMem& operator=(const DevMem&) = delete;
+};
+
+double now() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+}  // namespace
+
+void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd_result* R) {
+    chebfd_params p = p0;
+    CHEBFD_REQUIRE(p.ns >= 4 && p.ns <= 1024 && p.ns % 4 == 0, CHEBFD_EINVAL,
+                   "need 4 <= ns <= 1024, ns a multiple of 4");
+    CHEBFD_REQUIRE(p.Np >= 2, CHEBFD_EINVAL, "need Np >= 2");
+    CHEBFD_REQUIRE(p.lam_hi > p.lam_lo, CHEBFD_EINVAL, "need lam_hi > lam_lo");
+    CHEBFD_REQUIRE(p.eps > 0.0, CHEBFD_EINVAL, "need eps > 0");
+    if (p.mu <= 0.0) p.mu = 2.0;
+    if (p.max_iter <= 0) p.max_iter = 50;
+    if (p.lanczos_steps <= 0) p.lanczos_steps = 30;
+    const bool cplx = M.complex_values;
+    const chebfd_dtype d64 = cplx ? CHEBFD_C128 : CHEBFD_R64;
+    const chebfd_dtype d32 = cplx ? CHEBFD_C64 : CHEBFD_R32;
+    const bool mixed = p.precision == CHEBFD_PRECISION_MIXED;
+    CHEBFD_REQUIRE(!mixed || M.val32 != nullptr, CHEBFD_EINVAL,
+                   "mixed precision needs a matrix built with also_single");
+    if (p.nb <= 0) p.nb = cplx ? 64 : 128;
+    const double t_start = now();
+    double a = p.a, b = p.b;
+    if (!(b > a)) scale_bounds_impl(M, p.lanczos_steps, p.seed, &a, &b, s);
+    const double normH = std::max(std::fabs(a), std::fabs(b));
+    const double alpha = 2.0 / (b - a), beta = (a + b) / (a - b);
+    const std::vector<double> gc = coefficients(a, b, p.lam_lo, p.lam_hi, p.Np, p.kernel, p.mu);
+    const int64_t n = M.n;
+    const int ns = p.ns;
+    const int64_t ld = ns;  // rows start on 16 bytes in every precision (ns % 4 == 0)
+    DevMem Y64((size_t)n * ld * dtype_size(d64));
+    DevMem X32(mixed ? (size_t)n * ld * dtype_size(d32) : 0);
+    CHEBFD_CHECK_CUDA(cudaMemsetAsync(Y64.p, 0, (size_t)n * ld * dtype_size(d64), s));
+    launch_random_block(Y64.p, n, ld, ns, 0, ns, p.seed, d64, s);
+    bool single_phase = mixed;
+    if (mixed) convert_block_impl(Y64.p, d64, ld, X32.p, d32, ld, n, ns, s);
+
+    std::vector<double> theta(ns), res(ns), prev_theta, prev_res;
+    int64_t refill = 0;
+    double prev_worst = -1.0;
+    double t_filter = 0.0, t_dense = 0.0;
+    int it = 0, fp64_its = 0;
+    bool converged = false;
+    std::vector<int> acc_idx;
+    for (it = 1; it <= p.max_iter; ++it) {
+        // ---- step 5: filter
+        double t0 = now();
+        if (single_phase) {
+            filter_block_impl(M, alpha, beta, gc.data(), p.Np, X32.p, ld, ns, d32, nullptr, s, p.nb);
+            convert_block_impl(X32.p, d32, ld, Y64.p, d64, ld, n, ns, s);
+        } else {
+            filter_block_impl(M, alpha, beta, gc.data(), p.Np, Y64.p, ld, ns, d64, nullptr, s, p.nb);
+            ++fp64_its;
+        }
+        CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+        double t1 = now();
+        t_filter += t1 - t0;
+        // ---- steps 6-7: orthonormalise, Rayleigh-Ritz
+        orthonormalize_impl(Y64.p, n, ns, ld, d64, p.seed, &refill, nullptr, s);
+        rayleigh_ritz_impl(M, Y64.p, ld, ns, d64, theta.data(), res.data(), nullptr, s);
+        t_dense += now() - t1;
+        // ---- step 8: window membership, ghosts, convergence
+        acc_idx.clear();
+        for (int k = 0; k < ns; ++k) {
+            if (!(theta[k] >= p.lam_lo && theta[k] <= p.lam_hi)) continue;
+            bool ghost = false;
+            if (!prev_theta.empty()) {
+                int j = 0;
+                for (int q = 1; q < ns; ++q)
+                    if (std::fabs(prev_theta[q] - theta[k]) < std::fabs(prev_theta[j] - theta[k]))
+                        j = q;
+                ghost = res[k] > std::sqrt(p.eps) * normH && !(prev_res[j] >= 10.0 * res[k]);
+            }
+            if (!ghost) acc_idx.push_back(k);
+        }
+        double worst = 0.0;
+        for (int k : acc_idx) worst = std::max(worst, res[k]);
+        converged = !acc_idx.empty() && worst <= p.eps * normH;
+        if (converged && !single_phase) break;
+        if (converged && single_phase) {
+            // reached the target in single precision: confirm with one FP64 sweep
+            single_phase = false;
+        } else if (single_phase && prev_worst > 0.0 && worst > 1e-9 * normH &&
+                   worst > 0.5 * prev_worst) {
+            single_phase = false;  // residuals stalled at the single-precision floor
+        }
+        prev_worst = worst;
+        prev_theta = theta;
+        prev_res = res;
+        if (single_phase) convert_block_impl(Y64.p, d64, ld, X32.p, d32, ld, n, ns, s);
+    }
+    if (it > p.max_iter) it = p.max_iter;
+    // ---- collect the accepted pairs (ascending theta: already sorted)
+    const int nev = (int)acc_idx.size();
+    R->lambda.resize(nev);
+    R->res.resize(nev);
+    const size_t es = dtype_size(d64);
+    R->n = n;
+    R->elem_size = es;
+    if (nev > 0) {
+        CHEBFD_CHECK_CUDA(cudaMalloc(&R->V, (size_t)n * nev * es));
+        for (int q = 0; q < nev; ++q) {
+            const int k = acc_idx[q];
+            R->lambda[q] = theta[k];
+            R->res[q] = res[k];
+            CHEBFD_CHECK_CUDA(cudaMemcpy2DAsync((char*)R->V + q * es, nev * es,
+                                                (char*)Y64.p + k * es, ld * es, es, n,
+                                                cudaMemcpyDeviceToDevice, s));
+        }
+        CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    chebfd_result_info& I = R->info;
+    I.nev = nev;
+    I.iterations = it;
+    I.converged = converged ? 1 : 0;
+    I.fp64_iterations = fp64_its;
+    I.n_mvm = (int64_t)it * ns * p.Np;
+    I.a = a;
+    I.b = b;
+    I.seconds_filter = t_filter;
+    I.seconds_dense = t_dense;
+    I.seconds_total = now() - t_start;
+    I.lambda = R->lambda.data();
+    I.res = R->res.data();
+    I.V = R->V;
+}
+
+void orthonormalize_impl(void* Yv, int64_t n, int ns, int64_t ld, chebfd_dtype dt,
+                         uint64_t seed, int64_t* refill_counter, int* rank_out, cudaStream_t s);
+void residuals_impl(const Matrix& M, const void* V, const double* theta_host, int64_t ld, int k,
+                    chebfd_dtype dt, double* res_host, cudaStream_t s);
+
+}  // namespace chebfd
+
+using namespace chebfd;
+
+extern "C" {
+
+chebfd_status chebfd_orthonormalize(void* Y, int64_t n, int ns, int64_t ld, chebfd_dtype vdt,
+                                    uint64_t refill_seed, int64_t* refill_counter, int* rank,
+                                    void* stream) {
+    return guarded([&] {
+        orthonormalize_impl(Y, n, ns, ld, vdt, refill_seed, refill_counter, rank,
+                            as_stream(stream));
+    });
+}
+
+chebfd_status chebfd_rayleigh_ritz(const chebfd_matrix* H, void* Y, int64_t ld, int ns,
+                                   chebfd_dtype vdt, double* theta, double* res, void* HV,
+                                   void* stream) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(H, CHEBFD_EINVAL, "null matrix");
+        rayleigh_ritz_impl(H->m, Y, ld, ns, vdt, theta, res, HV, as_stream(stream));
+    });
+}
+
+chebfd_status chebfd_residuals(const chebfd_matrix* H, const void* V, const double* theta,
+                               int64_t ld, int k, chebfd_dtype vdt, double* res, void* stream) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(H, CHEBFD_EINVAL, "null matrix");
+        residuals_impl(H->m, V, theta, ld, k, vdt, res, as_stream(stream));
+    });
+}
+
+chebfd_status chebfd_convert_block(const void* X, chebfd_dtype xdt, int64_t ldx, void* Y,
+                                   chebfd_dtype ydt, int64_t ldy, int64_t n, int nb,
+                                   void* stream) {
+    return guarded(
+        [&] { convert_block_impl(X, xdt, ldx, Y, ydt, ldy, n, nb, as_stream(stream)); });
+}
+
+chebfd_status chebfd_solve(const chebfd_matrix* H, const chebfd_params* p, void* stream,
+                           chebfd_result** out) {
+    chebfd_result* R = nullptr;
+    chebfd_status st = guarded([&] {
+        CHEBFD_REQUIRE(H && p && out, CHEBFD_EINVAL, "null argument");
+        R = new chebfd_result();
+        solve_impl(H->m, *p, as_stream(stream), R);
+    });
+    if (st != CHEBFD_OK) {
+        if (R) {
+            cudaFree(R->V);
+            delete R;
+        }
+        return st;
+    }
+    *out = R;
+    if (!R->info.converged) {
+        set_error("ChebFD did not converge within max_iter iterations");
+        return CHEBFD_ENOCONV;
+    }
+    return CHEBFD_OK;
+}
+
+chebfd_status chebfd_result_get(const chebfd_result* r, chebfd_result_info* out) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(r && out, CHEBFD_EINVAL, "null argument");
+        *out = r->info;
+    });
+}
+
+chebfd_status chebfd_result_copy_vectors(const chebfd_result* r, void* dst, int64_t ld,
+                                         void* stream) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(r && (dst || r->info.nev == 0), CHEBFD_EINVAL, "null argument");
+        const int nev = r->info.nev;
+        CHEBFD_REQUIRE(ld >= nev, CHEBFD_EINVAL, "ld < nev");
+        if (nev == 0) return;
+        const size_t es = r->elem_size;
+        cudaStream_t s = as_stream(stream);
+        CHEBFD_CHECK_CUDA(cudaMemcpy2DAsync(dst, ld * es, r->V, nev * es, nev * es, r->n,
+                                            cudaMemcpyDeviceToDevice, s));
+        CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+chebfd_status chebfd_result_destroy(chebfd_result* r) {
+    return guarded([&] {
+        if (!r) return;
+        cudaFree(r->V);
+        delete r;
+    });
+}
+
+}  // extern "C"

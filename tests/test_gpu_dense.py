@@ -1,0 +1,134 @@
+"""Parity of the dense FP64 steps and of the whole ChebFD iteration (through the
+C ABI) with the CPU oracle and with dense diagonalisation."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1510_04895_gb300 as pkg
+from oracle import bounds as obounds, lattice, rr as orr, solve as osolve, svqb as osvqb
+from paper_1510_04895_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def span_distance(A, B):
+    """max-norm of B minus its projection onto span(A) (A, B orthonormal): zero
+    exactly when span(B) lies in span(A); linear in a perturbation of either."""
+    return float(np.abs(B - A @ (A.conj().T @ B)).max())
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+def test_orthonormalize_full_rank_matches_oracle(cplx):
+    Y0 = workloads.random_block(7, 3001 if cplx else 3000, 48, cplx)
+    Y0[:, 5] *= 1e-5
+    Y = torch.from_numpy(Y0).to(DEV)
+    rank, cnt = pkg.chebfd_orthonormalize(Y, seed=3)
+    Q = Y.cpu().numpy()
+    Qo, rank_o, cnt_o = osvqb.svqb(Y0, seed=3)
+    assert rank == rank_o == 48 and cnt == cnt_o == 0
+    assert np.abs(Q.conj().T @ Q - np.eye(48)).max() <= 1e-12
+    assert span_distance(Q, Qo) <= 1e-10
+
+
+def test_orthonormalize_rank_deficient_refills_like_oracle():
+    Y0 = workloads.random_block(8, 2000, 12, True)
+    Z = np.concatenate([Y0, Y0 @ workloads.random_block(9, 12, 8, True)], axis=1)  # rank 12 of 20
+    Y = torch.from_numpy(np.ascontiguousarray(Z)).to(DEV)
+    rank, cnt = pkg.chebfd_orthonormalize(Y, seed=5, refill_counter=3)
+    Qo, rank_o, cnt_o = osvqb.svqb(Z, seed=5, refill_counter=3)
+    assert rank == rank_o == 12 and cnt == cnt_o == 11
+    Q = Y.cpu().numpy()
+    assert np.abs(Q.conj().T @ Q - np.eye(20)).max() <= 1e-12
+    assert span_distance(Q, Qo) <= 1e-9
+
+
+@pytest.mark.parametrize("kind", ["topi", "graphene"])
+def test_rayleigh_ritz_matches_oracle(kind):
+    if kind == "topi":
+        H = pkg.chebfd_matrix_create_lattice("topi", 4, 5, 6, W=1.1, seed=4)
+        Ho = lattice.to_scipy(*lattice.topi_csr(4, 5, 6, W=1.1, seed=4))
+    else:
+        H = pkg.chebfd_matrix_create_lattice("graphene", 30, 20, W=1.0, seed=4)
+        Ho = lattice.to_scipy(*lattice.graphene_csr(30, 20, W=1.0, seed=4))
+    Y0, _, _ = osvqb.svqb(workloads.random_block(1, H.n, 32, H.is_complex))
+    Y = torch.from_numpy(np.ascontiguousarray(Y0)).to(DEV)
+    theta, res = pkg.chebfd_rayleigh_ritz(H, Y)
+    th_o, V_o, res_o = orr.rayleigh_ritz(Ho, Y0)
+    normH = abs(Ho).sum(axis=1).max()
+    assert np.abs(theta - th_o).max() <= 1e-12 * normH
+    assert np.abs(res - res_o).max() <= 1e-11 * normH
+    V = Y.cpu().numpy()
+    assert np.allclose(orr.residual_norms(Ho, V, theta), res, atol=1e-11 * normH)
+    r2 = pkg.chebfd_residuals(H, Y, theta)
+    assert np.allclose(r2, res, atol=1e-11 * normH)
+
+
+def test_rayleigh_ritz_exact_invariant_subspace():
+    H = pkg.chebfd_matrix_create_lattice("topi", 3, 3, 3, W=0.8, seed=9)
+    Ho = lattice.to_scipy(*lattice.topi_csr(3, 3, 3, W=0.8, seed=9))
+    lam, Vd = np.linalg.eigh(Ho.toarray())
+    Y = torch.from_numpy(np.ascontiguousarray(Vd[:, 40:52])).to(DEV)
+    theta, res = pkg.chebfd_rayleigh_ritz(H, Y)
+    assert np.abs(theta - lam[40:52]).max() <= 1e-12
+    assert res.max() <= 1e-12
+
+
+def test_convert_block_round_trip():
+    X0 = workloads.random_block(2, 1000, 16, True)
+    X = torch.from_numpy(X0).to(DEV)
+    Y = torch.empty((1000, 16), dtype=torch.complex64, device=DEV)
+    pkg.chebfd_convert_block(X, Y)
+    assert np.array_equal(Y.cpu().numpy(), X0.astype(np.complex64))
+    Z = torch.empty_like(X)
+    pkg.chebfd_convert_block(Y, Z)
+    assert np.array_equal(Z.cpu().numpy(), X0.astype(np.complex64).astype(np.complex128))
+
+
+def _dense_window(Ho, lo, hi):
+    e = np.linalg.eigvalsh(Ho.toarray())
+    return e[(e >= lo) & (e <= hi)], e
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_smallest_insulator_against_dense(precision):
+    """8x8x8x4 insulator (N = 2048), W = 0.5, window [-0.1, 0.1], n_s = 64,
+    N_p = 200, Jackson: all window eigenvalues within 1e-10 ||H|| of the dense
+    eigensolver, residuals <= 1e-9 ||H||, chiral +- pairing."""
+    w = workloads.TOPI_SMALL
+    H = pkg.chebfd_matrix_create_lattice("topi", 8, 8, 8, t=1.0, m=1.0, W=0.5, seed=0,
+                                         also_single=True)
+    Ho = lattice.to_scipy(*lattice.topi_csr(8, 8, 8, t=1.0, m=1.0, W=0.5, seed=0))
+    r = pkg.chebfd_solve(H, -0.1, 0.1, 64, 200, eps=1e-9, kernel="jackson", precision=precision)
+    ew, e = _dense_window(Ho, -0.1, 0.1)
+    normH = max(abs(r["a"]), abs(r["b"]))
+    assert r["converged"] and r["nev"] == len(ew) > 0
+    assert np.abs(np.sort(r["lam"]) - ew).max() <= 1e-10 * normH
+    assert r["res"].max() <= 1e-9 * normH
+    V = r["V"].cpu().numpy()
+    assert np.abs(V.conj().T @ V - np.eye(r["nev"])).max() <= 1e-12
+    assert np.abs(orr.residual_norms(Ho, V, r["lam"])).max() <= 1e-9 * normH
+    th = np.sort(r["lam"])
+    assert np.abs(th + th[::-1]).max() <= 1e-10 * normH
+    if precision == "mixed":
+        assert 1 <= r["fp64_iterations"] < r["iterations"]
+    # the oracle run on the same workload finds the same eigenvalues
+    ro = osolve.chebfd(Ho, r["a"], r["b"], -0.1, 0.1, 64, 200, 1e-9, kind="jackson", seed=0)
+    assert np.abs(np.sort(ro["theta"]) - th).max() <= 1e-10 * normH
+
+
+def test_solve_graphene_real_against_dense():
+    H = pkg.chebfd_matrix_create_lattice("graphene", 40, 36, W=1.0, seed=2, also_single=True)
+    Ho = lattice.to_scipy(*lattice.graphene_csr(40, 36, W=1.0, seed=2))
+    r = pkg.chebfd_solve(H, -0.05, 0.05, 48, 400, eps=1e-9, kernel="lanczos", precision="mixed")
+    ew, _ = _dense_window(Ho, -0.05, 0.05)
+    normH = max(abs(r["a"]), abs(r["b"]))
+    assert r["converged"] and r["nev"] == len(ew) > 0
+    assert np.abs(np.sort(r["lam"]) - ew).max() <= 1e-10 * normH
+    assert r["res"].max() <= 1e-9 * normH
+
+
+def test_solve_reports_no_convergence():
+    H = pkg.chebfd_matrix_create_lattice("topi", 4, 4, 4, W=0.5, seed=0)
+    r = pkg.chebfd_solve(H, -0.2, 0.2, 16, 20, eps=1e-12, kernel="jackson", max_iter=1)
+    assert r["status"] == "ENOCONV" and not r["converged"] and r["iterations"] == 1
