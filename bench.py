@@ -57,15 +57,24 @@ def workload_params(args):
 
 
 def read_traffic():
-    """DRAM bytes per launch of the fused step from the committed ncu summary."""
+    """DRAM bytes per launch of the fused step from the committed ncu summary,
+    or None when the kernel source changed since that capture."""
+    import hashlib
+    vals = {}
     try:
         with open(PROFILE_TRAFFIC) as f:
             for line in f:
-                if line.startswith("traffic_bytes_per_launch"):
-                    return float(line.split()[1])
+                if line.strip() and not line.startswith("#"):
+                    parts = line.split()
+                    vals[parts[0]] = parts[1] if len(parts) > 1 else ""
+        src = os.path.join(ROOT, "paper_1510_04895_gb300", "csrc", "filter_kernels.cuh")
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
     except OSError:
-        pass
-    return None
+        return None
+    if vals.get("kernel_source_sha256_16") != digest:
+        return None
+    return float(vals["traffic_bytes_per_launch"])
 
 
 def measured_peaks():

@@ -122,7 +122,6 @@ struct StepArgs {
 // Launch one step kernel.  dt selects the vector type, `single` the matrix copy.
 void launch_step(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs& a,
                  cudaStream_t stream);
-int step_grid_size(const Matrix& M, chebfd_dtype dt, int nb);
 int max_panel_width(chebfd_dtype dt);
 
 void launch_random_block(void* X, int64_t n, int64_t ld, int nb, int col0, int ns_total,

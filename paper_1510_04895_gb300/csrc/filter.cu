@@ -15,11 +15,6 @@ void launch_step_f32(const SellView& H, bool cplx, StepMode mode, const StepArgs
 
 namespace {
 
-int env_int(const char* name, int dflt) {
-    const char* v = getenv(name);
-    return v ? atoi(v) : dflt;
-}
-
 SellView view_of(const Matrix& M, bool single) {
     SellView v;
     v.chunk_ptr = M.chunk_ptr;
@@ -49,16 +44,6 @@ int max_panel_width(chebfd_dtype dt) {
     return 0;
 }
 
-int step_grid_size(const Matrix& M, chebfd_dtype, int) {
-    // Persistent grid: whole waves of resident blocks on every SM.  The block
-    // count per SM is bounded by 2048 threads / 256 and by the CHEBFD_STEP_BPS
-    // override used by the autotuner.
-    int bps = env_int("CHEBFD_STEP_BPS", 4);
-    if (bps < 1) bps = 1;
-    if (bps > 8) bps = 8;
-    return M.num_sms * bps;
-}
-
 void validate_block(const Matrix& M, chebfd_dtype dt, const void* X, int64_t ld, int nb) {
     CHEBFD_REQUIRE(X != nullptr, CHEBFD_EINVAL, "null block pointer");
     CHEBFD_REQUIRE(nb >= 1 && ld >= nb, CHEBFD_EINVAL, "need 1 <= nb <= ld");
@@ -78,11 +63,11 @@ void launch_step(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs
     const int wc = chunks_per_row(dt, a.nb);
     CHEBFD_REQUIRE(wc >= 1 && wc <= 64, CHEBFD_EINVAL, "panel too wide for one row group");
     const SellView v = view_of(M, is_single(dt));
-    const int grid = step_grid_size(M, dt, a.nb);
+    // persistent grid: resident blocks per SM (occupancy) x SM count
     if (is_single(dt))
-        launch_step_f32(v, is_complex(dt), mode, a, wc, grid, stream);
+        launch_step_f32(v, is_complex(dt), mode, a, wc, M.num_sms, stream);
     else
-        launch_step_f64(v, is_complex(dt), mode, a, wc, grid, stream);
+        launch_step_f64(v, is_complex(dt), mode, a, wc, M.num_sms, stream);
     CHEBFD_CHECK_CUDA(cudaGetLastError());
 }
 

@@ -99,14 +99,37 @@ struct SellView {
 
 constexpr int STEP_THREADS = 256;
 
+template <class R, bool CPLX>
+__device__ __forceinline__ typename ValT<R, CPLX>::type shfl_val(
+    const typename ValT<R, CPLX>::type& v, int src, int width) {
+    if constexpr (CPLX) {
+        typename ValT<R, CPLX>::type o;
+        o.x = __shfl_sync(0xffffffffu, v.x, src, width);
+        o.y = __shfl_sync(0xffffffffu, v.y, src, width);
+        return o;
+    } else {
+        return __shfl_sync(0xffffffffu, v, src, width);
+    }
+}
+
+// Entries of one row handled per batch: all gathers of a batch are issued
+// back to back (one memory latency per batch instead of one per entry).
+template <int CPT>
+struct Batch {
+    static constexpr int EB = CPT == 1 ? 16 : 8;
+};
+
 template <class R, bool CPLX, int G, int CPT, int MODE>
-__global__ void __launch_bounds__(STEP_THREADS)
+__global__ void __launch_bounds__(STEP_THREADS, 2)
     cheb_step_kernel(SellView H, StepArgs a, int wc) {
     using V = typename ValT<R, CPLX>::type;
     using Chunk = ChunkT<R>;
     constexpr int K = Chunk::K;
     constexpr int CPC = CPLX ? K / 2 : K;  // vector columns per chunk
     constexpr int SLOTS = STEP_THREADS / G;
+    constexpr int EB = Batch<CPT>::EB;
+    constexpr int EPL = (EB + G - 1) / G;  // entries loaded per lane per batch
+    constexpr unsigned FULL = 0xffffffffu;
 
     const V* __restrict__ val = reinterpret_cast<const V*>(H.val);
     const int32_t* __restrict__ colp = H.col;
@@ -132,12 +155,29 @@ __global__ void __launch_bounds__(STEP_THREADS)
         for (int c = 0; c < CPC; ++c) dot_a[q][c] = dot_b[q][c] = (R)0;
 
     const int64_t nslots = (int64_t)gridDim.x * SLOTS;
-    for (int64_t r = (int64_t)blockIdx.x * SLOTS + slot; r < H.n; r += nslots) {
-        const int64_t k = r / H.C;
-        const int l = (int)(r - k * H.C);
-        const int64_t base = __ldg(H.chunk_ptr + k) + l;
-        const int len = __ldg(H.chunk_len + k);
-        const int64_t orig = H.perm ? __ldg(H.perm + r) : r;
+    // Warp-uniform loop: every lane runs the same iterations so the shuffles
+    // below always see the full warp; groups past the last row are inactive.
+    for (int64_t r = (int64_t)blockIdx.x * SLOTS + slot; __any_sync(FULL, r < H.n); r += nslots) {
+        const bool active = r < H.n;
+        int64_t base = 0, orig = 0;
+        int len = 0;
+        if (active) {
+            const int64_t k = r / H.C;
+            base = __ldg(H.chunk_ptr + k) + (r - k * H.C);
+            len = __ldg(H.chunk_len + k);
+            orig = H.perm ? __ldg(H.perm + r) : r;
+        }
+        // own-row streams, issued before the gathers so their latency overlaps
+        Chunk uo[CPT], xo[CPT];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int ci = lane + q * G;
+            const bool on = active && ci < wc;
+            const int64_t cofs = (int64_t)ci * K;
+            if (on) uo[q] = load_chunk_ldg(u + orig * ldg + cofs);
+            if (MODE == MODE_SECOND && on) xo[q] = load_chunk_cs(y + orig * ldy + cofs);
+            if (MODE == MODE_STEP && on) xo[q] = load_chunk_cs(w + orig * ldw + cofs);
+        }
 
         Chunk acc[CPT];
 #pragma unroll
@@ -145,49 +185,74 @@ __global__ void __launch_bounds__(STEP_THREADS)
 #pragma unroll
             for (int c = 0; c < K; ++c) acc[q].v[c] = (R)0;
 
-#pragma unroll 4
-        for (int j = 0; j < len; ++j) {
-            const int64_t pos = base + (int64_t)j * H.C;
-            const int64_t cj = __ldg(colp + pos);
-            const V vj = val[pos];
-            const R* urow = u + cj * ldg;
+        const int maxlen = __reduce_max_sync(FULL, len);
+        for (int j0 = 0; j0 < maxlen; j0 += EB) {
+            // the group's lanes load the batch's column indices and values together
+            int32_t mc[EPL];
+            V mv[EPL];
 #pragma unroll
-            for (int q = 0; q < CPT; ++q) {
-                const int ci = lane + q * G;
-                if (ci < wc) mac<R, CPLX>(acc[q], vj, load_chunk_ldg(urow + (int64_t)ci * K));
+            for (int e = 0; e < EPL; ++e) {
+                const int j = j0 + lane + e * G;
+                if (j < len) {
+                    const int64_t pos = base + (int64_t)j * H.C;
+                    mc[e] = __ldcs(colp + pos);
+                    mv[e] = __ldcs(val + pos);
+                } else {
+                    mc[e] = (int32_t)orig;
+                    mv[e] = V{};
+                }
+            }
+            // issue every gather of the batch, then accumulate
+            Chunk g[EB][CPT];
+#pragma unroll
+            for (int e = 0; e < EB; ++e) {
+                const int cj = __shfl_sync(FULL, mc[e / G], e % G, G);
+                const R* urow = u + (int64_t)cj * ldg;
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) {
+                    const int ci = lane + q * G;
+                    if (j0 + e < len && ci < wc)
+                        g[e][q] = load_chunk_ldg(urow + (int64_t)ci * K);
+                    else
+#pragma unroll
+                        for (int c = 0; c < K; ++c) g[e][q].v[c] = (R)0;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < EB; ++e) {
+                const V vj = shfl_val<R, CPLX>(mv[e / G], e % G, G);
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) mac<R, CPLX>(acc[q], vj, g[e][q]);
             }
         }
 
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
             const int ci = lane + q * G;
-            if (ci >= wc) continue;
+            if (!active || ci >= wc) continue;
             const int64_t cofs = (int64_t)ci * K;
-            const Chunk uo = load_chunk_ldg(u + orig * ldg + cofs);
             R* wp = w + orig * ldw + cofs;
             R* yp = y + orig * ldy + cofs;
             Chunk wn;
             if (MODE == MODE_SPMV) {
 #pragma unroll
-                for (int c = 0; c < K; ++c) wn.v[c] = fma(alpha, acc[q].v[c], beta * uo.v[c]);
+                for (int c = 0; c < K; ++c) wn.v[c] = fma(alpha, acc[q].v[c], beta * uo[q].v[c]);
                 store_chunk_cs(wp, wn);
             } else if (MODE == MODE_SECOND) {
-                const Chunk xo = load_chunk_cs(yp);
                 Chunk yn;
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
-                    wn.v[c] = fma(two_alpha, acc[q].v[c], fma(two_beta, uo.v[c], -xo.v[c]));
-                    yn.v[c] = fma(c2, wn.v[c], fma(c1, uo.v[c], c0 * xo.v[c]));
+                    wn.v[c] = fma(two_alpha, acc[q].v[c], fma(two_beta, uo[q].v[c], -xo[q].v[c]));
+                    yn.v[c] = fma(c2, wn.v[c], fma(c1, uo[q].v[c], c0 * xo[q].v[c]));
                 }
                 store_chunk_cs(wp, wn);
                 store_chunk_cs(yp, yn);
             } else {
-                const Chunk wo = load_chunk_cs(wp);
                 const Chunk yo = load_chunk_cs(yp);
                 Chunk yn;
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
-                    wn.v[c] = fma(two_alpha, acc[q].v[c], fma(two_beta, uo.v[c], -wo.v[c]));
+                    wn.v[c] = fma(two_alpha, acc[q].v[c], fma(two_beta, uo[q].v[c], -xo[q].v[c]));
                     yn.v[c] = fma(c0, wn.v[c], yo.v[c]);
                 }
                 store_chunk_cs(wp, wn);
@@ -197,12 +262,12 @@ __global__ void __launch_bounds__(STEP_THREADS)
 #pragma unroll
                 for (int c = 0; c < CPC; ++c) {
                     if constexpr (CPLX) {
-                        const R ur = uo.v[2 * c], ui = uo.v[2 * c + 1];
+                        const R ur = uo[q].v[2 * c], ui = uo[q].v[2 * c + 1];
                         dot_a[q][c] = fma(ur, ur, fma(ui, ui, dot_a[q][c]));
                         dot_b[q][c] = fma(ur, wn.v[2 * c], fma(ui, wn.v[2 * c + 1], dot_b[q][c]));
                     } else {
-                        dot_a[q][c] = fma(uo.v[c], uo.v[c], dot_a[q][c]);
-                        dot_b[q][c] = fma(uo.v[c], wn.v[c], dot_b[q][c]);
+                        dot_a[q][c] = fma(uo[q].v[c], uo[q].v[c], dot_a[q][c]);
+                        dot_b[q][c] = fma(uo[q].v[c], wn.v[c], dot_b[q][c]);
                     }
                 }
             }

@@ -1,48 +1,65 @@
 // Instantiations of the fused Chebyshev step kernel for float vectors.
+#include <cstdlib>
+
 #include "filter_kernels.cuh"
 
 namespace chebfd {
 
 namespace {
 
-template <bool CPLX, int G, int CPT>
-void launch_g(const SellView& H, StepMode mode, const StepArgs& a, int wc,
-              int grid, cudaStream_t s) {
+// Resident blocks per SM of one instantiation (occupancy API, cached), capped
+// by CHEBFD_STEP_BPS when set: the persistent grid is whole waves.
+template <class Kern>
+int blocks_per_sm(Kern kern, size_t smem) {
+    static int cached[2] = {0, 0};
+    int& occ = cached[smem ? 1 : 0];
+    if (!occ) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, STEP_THREADS, smem) !=
+                cudaSuccess || occ < 1)
+            occ = 1;
+    }
+    int b = occ;
+    if (const char* e = getenv("CHEBFD_STEP_BPS")) b = std::max(1, std::min(b, atoi(e)));
+    return std::min(b, 8);
+}
+
+template <bool CPLX, int G, int CPT, int MODE>
+void launch_m(const SellView& H, const StepArgs& a, int wc, int sms, cudaStream_t s) {
     constexpr int SLOTS = STEP_THREADS / G;
-    constexpr int CPC = CPLX ? ChunkT<float>::K / 2 : ChunkT<float>::K;
-    (void)CPC;
     const size_t smem = a.moments ? (size_t)SLOTS * 2 * a.nb * sizeof(double) : 0;
+    auto kern = cheb_step_kernel<float, CPLX, G, CPT, MODE>;
+    const int grid = sms * blocks_per_sm(kern, a.moments ? (size_t)16384 : 0);
+    kern<<<grid, STEP_THREADS, smem, s>>>(H, a, wc);
+}
+
+template <bool CPLX, int G, int CPT>
+void launch_g(const SellView& H, StepMode mode, const StepArgs& a, int wc, int sms,
+              cudaStream_t s) {
     switch (mode) {
-        case MODE_SPMV:
-            cheb_step_kernel<float, CPLX, G, CPT, MODE_SPMV><<<grid, STEP_THREADS, smem, s>>>(H, a, wc);
-            break;
-        case MODE_SECOND:
-            cheb_step_kernel<float, CPLX, G, CPT, MODE_SECOND><<<grid, STEP_THREADS, smem, s>>>(H, a, wc);
-            break;
-        case MODE_STEP:
-            cheb_step_kernel<float, CPLX, G, CPT, MODE_STEP><<<grid, STEP_THREADS, smem, s>>>(H, a, wc);
-            break;
+        case MODE_SPMV: launch_m<CPLX, G, CPT, MODE_SPMV>(H, a, wc, sms, s); break;
+        case MODE_SECOND: launch_m<CPLX, G, CPT, MODE_SECOND>(H, a, wc, sms, s); break;
+        case MODE_STEP: launch_m<CPLX, G, CPT, MODE_STEP>(H, a, wc, sms, s); break;
     }
 }
 
 template <bool CPLX>
-void launch_c(const SellView& H, StepMode mode, const StepArgs& a, int wc, int grid,
+void launch_c(const SellView& H, StepMode mode, const StepArgs& a, int wc, int sms,
               cudaStream_t s) {
-    if (wc > 32) launch_g<CPLX, 32, 2>(H, mode, a, wc, grid, s);
-    else if (wc > 16) launch_g<CPLX, 32, 1>(H, mode, a, wc, grid, s);
-    else if (wc > 8) launch_g<CPLX, 16, 1>(H, mode, a, wc, grid, s);
-    else if (wc > 4) launch_g<CPLX, 8, 1>(H, mode, a, wc, grid, s);
-    else if (wc > 2) launch_g<CPLX, 4, 1>(H, mode, a, wc, grid, s);
-    else if (wc > 1) launch_g<CPLX, 2, 1>(H, mode, a, wc, grid, s);
-    else launch_g<CPLX, 1, 1>(H, mode, a, wc, grid, s);
+    if (wc > 32) launch_g<CPLX, 32, 2>(H, mode, a, wc, sms, s);
+    else if (wc > 16) launch_g<CPLX, 32, 1>(H, mode, a, wc, sms, s);
+    else if (wc > 8) launch_g<CPLX, 16, 1>(H, mode, a, wc, sms, s);
+    else if (wc > 4) launch_g<CPLX, 8, 1>(H, mode, a, wc, sms, s);
+    else if (wc > 2) launch_g<CPLX, 4, 1>(H, mode, a, wc, sms, s);
+    else if (wc > 1) launch_g<CPLX, 2, 1>(H, mode, a, wc, sms, s);
+    else launch_g<CPLX, 1, 1>(H, mode, a, wc, sms, s);
 }
 
 }  // namespace
 
 void launch_step_f32(const SellView& H, bool cplx, StepMode mode, const StepArgs& a, int wc,
-                    int grid, cudaStream_t s) {
-    if (cplx) launch_c<true>(H, mode, a, wc, grid, s);
-    else launch_c<false>(H, mode, a, wc, grid, s);
+                    int sms, cudaStream_t s) {
+    if (cplx) launch_c<true>(H, mode, a, wc, sms, s);
+    else launch_c<false>(H, mode, a, wc, sms, s);
 }
 
 }  // namespace chebfd
