@@ -198,6 +198,30 @@ chebfd_status chebfd_filter_block(const chebfd_matrix* H, double alpha, double b
                                   const double* gc, int Np, void* X, int64_t ld, int nb,
                                   chebfd_dtype vdt, double* moments, void* stream);
 
+/* Same contract and results as chebfd_filter_block, for callers that cannot
+ * allocate device memory at this point: for instance code that runs while
+ * another framework owns the device's memory through its own pool (a raw
+ * allocation there can fail or split that pool), or a latency-critical loop
+ * that must not pay for an allocation or the synchronisation it may imply.
+ * The paper has no counterpart of this entry point.
+ * The two work vectors and the moment reduction buffers live in one fixed
+ * device array of 68 MiB (64 MiB for the work vectors, 4 MiB of moment
+ * partials, 256 bytes of counters) that every GPU loading the library keeps
+ * until the process exits; the call itself allocates nothing.  Limit: the work
+ * vectors need 2 * N * w * element_size bytes, w = the panel width (n_b
+ * rounded up to 16 bytes, at most 64 complex / 128 real columns), so N * w <=
+ * 4M complex64 or real-double entries (e.g. N = 65536 at n_b = 64 complex64);
+ * larger requests return CHEBFD_EINVAL with a message naming the sizes.
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls on a device share the array and it keeps the last call's
+ * contents (the counters are cleared on every call): calls whose device work
+ * overlaps, from two streams or two host threads, race and must be
+ * serialised by the caller.  With moments != NULL the call synchronizes. */
+chebfd_status chebfd_filter_block_noalloc(const chebfd_matrix* H, double alpha, double beta,
+                                          const double* gc, int Np, void* X, int64_t ld, int nb,
+                                          chebfd_dtype vdt, double* moments, void* stream);
+
 /* One fused Chebyshev step of Fig. ChebFD (the kernel that carries the filter,
  * lines "w = 2(alpha H + beta) u - w ; x = x + g_n c_n w"): W <- 2(alpha H +
  * beta) U - W and Y <- Y + c W in one pass, for device blocks U, W, Y of shape

@@ -65,6 +65,9 @@ SIGNATURES = {
     "chebfd_filter_block": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double, c_dp,
                                            ctypes.c_int, c_vp, ctypes.c_int64, ctypes.c_int,
                                            ctypes.c_int, c_dp, c_vp]),
+    "chebfd_filter_block_noalloc": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double, c_dp,
+                                                   ctypes.c_int, c_vp, ctypes.c_int64,
+                                                   ctypes.c_int, ctypes.c_int, c_dp, c_vp]),
     "chebfd_chebyshev_step": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, c_vp, c_vp, c_vp, ctypes.c_int64,
                                              ctypes.c_int, ctypes.c_int, c_vp]),
@@ -260,6 +263,18 @@ def chebfd_filter_block(H, alpha, beta, gc, X, moments=None, stream=None):
     _check(lib().chebfd_filter_block(H.handle, alpha, beta, gc.ctypes.data_as(c_dp), Np, _ptr(X),
                                      X.stride(0), nb, dtype_of(X), mp, _stream(stream)),
            "chebfd_filter_block")
+
+
+def chebfd_filter_block_noalloc(H, alpha, beta, gc, X, moments=None, stream=None):
+    """As chebfd_filter_block, with the library's fixed device scratch instead of
+    allocated work vectors (for callers that cannot allocate device memory)."""
+    gc = np.ascontiguousarray(gc, np.float64)
+    Np = len(gc) - 1
+    n, nb = X.shape[0], X.shape[1]
+    mp = ctypes.cast(ctypes.c_void_p(moments.data_ptr()), c_dp) if moments is not None else None
+    _check(lib().chebfd_filter_block_noalloc(H.handle, alpha, beta, gc.ctypes.data_as(c_dp), Np,
+                                             _ptr(X), X.stride(0), nb, dtype_of(X), mp,
+                                             _stream(stream)), "chebfd_filter_block_noalloc")
 
 
 def chebfd_chebyshev_step(H, alpha, beta, c, U, W, Y, stream=None):
