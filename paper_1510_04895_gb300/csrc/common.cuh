@@ -76,6 +76,7 @@ struct Matrix {
     int64_t nchunks = 0;
     int C = 1, sigma = 1;
     int max_row_len = 0;
+    int uniform_width = 0;  // > 0: every chunk has this width (ELLPACK shape)
     bool complex_values = false;
     bool identity_perm = true;
     int64_t* chunk_ptr = nullptr;  // [nchunks+1]
@@ -117,6 +118,7 @@ struct StepArgs {
     double* moments;     // [2*Np x mom_ld]; nullptr = no dots
     int64_t mom_ld;
     int mom_step;        // n of the step: writes mu_{2n-2}, mu_{2n-1} (SPMV: mu_0, mu_1)
+    int tile;            // consecutive row groups per block and wave (0 = 1)
 };
 
 // Launch one step kernel.  dt selects the vector type, `single` the matrix copy.

@@ -9,9 +9,9 @@
 namespace chebfd {
 
 void launch_step_f64(const SellView& H, bool cplx, StepMode mode, const StepArgs& a, int wc,
-                     int grid, cudaStream_t s);
+                     int width, int sms, cudaStream_t s);
 void launch_step_f32(const SellView& H, bool cplx, StepMode mode, const StepArgs& a, int wc,
-                     int grid, cudaStream_t s);
+                     int width, int sms, cudaStream_t s);
 
 namespace {
 
@@ -36,7 +36,7 @@ int max_panel_width(chebfd_dtype dt) {
     // 64 chunks of 16 bytes per row group: 64 complex doubles, 128 complex floats,
     // 128 doubles, 256 floats; kept at 64 / 128 to bound register use.
     switch (dt) {
-        case CHEBFD_C128: return 64;
+        case CHEBFD_C128: return 32;  // FP64-ALU bound: narrower panels keep the fast path
         case CHEBFD_C64: return 64;
         case CHEBFD_R64: return 128;
         case CHEBFD_R32: return 128;
@@ -63,11 +63,19 @@ void launch_step(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs
     const int wc = chunks_per_row(dt, a.nb);
     CHEBFD_REQUIRE(wc >= 1 && wc <= 64, CHEBFD_EINVAL, "panel too wide for one row group");
     const SellView v = view_of(M, is_single(dt));
+    StepArgs args = a;
+    if (args.tile <= 0) {
+        static const int env_tile = [] {
+            const char* e = getenv("CHEBFD_STEP_TILE");
+            return e ? std::max(1, atoi(e)) : 4;
+        }();
+        args.tile = env_tile;
+    }
     // persistent grid: resident blocks per SM (occupancy) x SM count
     if (is_single(dt))
-        launch_step_f32(v, is_complex(dt), mode, a, wc, M.num_sms, stream);
+        launch_step_f32(v, is_complex(dt), mode, args, wc, M.uniform_width, M.num_sms, stream);
     else
-        launch_step_f64(v, is_complex(dt), mode, a, wc, M.num_sms, stream);
+        launch_step_f64(v, is_complex(dt), mode, args, wc, M.uniform_width, M.num_sms, stream);
     CHEBFD_CHECK_CUDA(cudaGetLastError());
 }
 

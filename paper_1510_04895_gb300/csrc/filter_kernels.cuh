@@ -5,17 +5,29 @@
 //   MODE_SPMV   : w = (alpha H + beta) u                       (also the first step)
 //   MODE_SECOND : w = 2 (alpha H + beta) u - x ; x = c0 x + c1 u + c2 w
 //   MODE_STEP   : w = 2 (alpha H + beta) u - w ; y = y + c0 w
-// optionally with the per-column dot products <u,u>, <u,w> (SPMV: <u,u>,
-// <u,w>) that give the Chebyshev moments of Sec. 4.
+// optionally with the per-column dot products <u,u>, <u,w> that give the
+// Chebyshev moments of Sec. 4.
 //
-// Mapping: a group of G consecutive threads owns one matrix row (in SELL
+// Mapping.  A group of G consecutive threads owns one matrix row (in SELL
 // order); each thread owns CPT 16-byte chunks of the row's nb vector entries,
 // so every gather of a neighbour row u_j is a contiguous, fully coalesced
-// nb*S_v-byte segment read with 128-bit loads.  The row's column indices and
-// values are read once per step for the whole block (broadcast inside the
-// group).  Thread blocks are persistent and stride over the rows, so all SMs
-// sweep the matrix as one front and the gathered rows of u are reused from L2.
+// nb*S_v-byte read with 128-bit loads.  The row's column indices and values
+// are loaded once per step for the whole block, cooperatively by the group,
+// and broadcast with warp shuffles; all gathers of the row are then issued
+// back to back.  All blocks sweep the rows as one front (a block takes a tile
+// of consecutive row groups per wave), so the rows a lattice row gathers
+// (same site, +-x neighbours) are mostly just read by the same block and hit
+// in L1, and the far ones (+-y, +-z) were read by other SMs a moment earlier
+// and hit in L2: u is read from DRAM about once per step.
+//
+// Fixed-width path (template L > 0): when every SELL chunk has the same width
+// L (ELLPACK shape, no padding), row offsets need no metadata loads and the
+// next row's indices/values are prefetched while the current row's gathers
+// are in flight: one memory latency per row.  FP32 complex/real arithmetic
+// uses the paired FMA of sm_100+ (__ffma2_rn).
 #pragma once
+
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -45,6 +57,11 @@ template <class R>
 __device__ __forceinline__ void store_chunk_cs(R* p, const ChunkT<R>& c) {
     __stcs(reinterpret_cast<uint4*>(p), *reinterpret_cast<const uint4*>(c.v));
 }
+template <class R>
+__device__ __forceinline__ void zero_chunk(ChunkT<R>& c) {
+#pragma unroll
+    for (int i = 0; i < ChunkT<R>::K; ++i) c.v[i] = (R)0;
+}
 
 template <class R, bool CPLX>
 struct ValT;
@@ -65,25 +82,110 @@ struct ValT<float, false> {
     using type = float;
 };
 
+// Accumulator of one 16-byte chunk of sum_j H_ij u_j.  Complex values keep two
+// partial sums, P = sum Re(h) (ur, ui) and Q = sum Im(h) (ur, ui); the complex
+// product is formed once at the end, (P.x - Q.y, P.y + Q.x).  In FP32 each
+// complex entry then costs two paired FMAs.
 template <class R, bool CPLX>
-__device__ __forceinline__ void mac(ChunkT<R>& acc, const typename ValT<R, CPLX>::type& v,
-                                    const ChunkT<R>& u) {
-    constexpr int K = ChunkT<R>::K;
-    if constexpr (CPLX) {
+struct Acc {
+    ChunkT<R> p, q;
+    __device__ __forceinline__ void zero() {
+        zero_chunk(p);
+        if (CPLX) zero_chunk(q);
+    }
+    __device__ __forceinline__ void mac(const typename ValT<R, CPLX>::type& h,
+                                        const ChunkT<R>& u) {
+        constexpr int K = ChunkT<R>::K;
+        if constexpr (std::is_same<R, float>::value) {
+            float2* P = reinterpret_cast<float2*>(p.v);
+            float2* Q = reinterpret_cast<float2*>(q.v);
+            const float2* U = reinterpret_cast<const float2*>(u.v);
+            if constexpr (CPLX) {
+                const float2 hr = make_float2(h.x, h.x), hi = make_float2(h.y, h.y);
 #pragma unroll
-        for (int c = 0; c < K / 2; ++c) {
-            const R ur = u.v[2 * c], ui = u.v[2 * c + 1];
-            R ar = acc.v[2 * c], ai = acc.v[2 * c + 1];
-            ar = fma(v.x, ur, ar);
-            ar = fma(-v.y, ui, ar);
-            ai = fma(v.x, ui, ai);
-            ai = fma(v.y, ur, ai);
-            acc.v[2 * c] = ar;
-            acc.v[2 * c + 1] = ai;
+                for (int c = 0; c < K / 2; ++c) {
+                    P[c] = __ffma2_rn(hr, U[c], P[c]);
+                    Q[c] = __ffma2_rn(hi, U[c], Q[c]);
+                }
+            } else {
+                const float2 hh = make_float2(h, h);
+#pragma unroll
+                for (int c = 0; c < K / 2; ++c) P[c] = __ffma2_rn(hh, U[c], P[c]);
+            }
+        } else {
+            if constexpr (CPLX) {
+#pragma unroll
+                for (int c = 0; c < K / 2; ++c) {
+                    p.v[2 * c] = fma(h.x, u.v[2 * c], p.v[2 * c]);
+                    p.v[2 * c + 1] = fma(h.x, u.v[2 * c + 1], p.v[2 * c + 1]);
+                    q.v[2 * c] = fma(h.y, u.v[2 * c], q.v[2 * c]);
+                    q.v[2 * c + 1] = fma(h.y, u.v[2 * c + 1], q.v[2 * c + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < K; ++c) p.v[c] = fma(h, u.v[c], p.v[c]);
+            }
         }
+    }
+    __device__ __forceinline__ ChunkT<R> value() const {
+        if constexpr (!CPLX) {
+            return p;
+        } else {
+            ChunkT<R> r;
+#pragma unroll
+            for (int c = 0; c < ChunkT<R>::K / 2; ++c) {
+                r.v[2 * c] = p.v[2 * c] - q.v[2 * c + 1];
+                r.v[2 * c + 1] = p.v[2 * c + 1] + q.v[2 * c];
+            }
+            return r;
+        }
+    }
+};
+
+// d = a * x + y on chunks (paired FMA for FP32).
+template <class R>
+__device__ __forceinline__ ChunkT<R> axpy_chunk(R a, const ChunkT<R>& x, const ChunkT<R>& y) {
+    ChunkT<R> d;
+    if constexpr (std::is_same<R, float>::value) {
+        const float2 aa = make_float2(a, a);
+        const float2* X = reinterpret_cast<const float2*>(x.v);
+        const float2* Y = reinterpret_cast<const float2*>(y.v);
+        float2* D = reinterpret_cast<float2*>(d.v);
+#pragma unroll
+        for (int c = 0; c < ChunkT<R>::K / 2; ++c) D[c] = __ffma2_rn(aa, X[c], Y[c]);
     } else {
 #pragma unroll
-        for (int c = 0; c < K; ++c) acc.v[c] = fma(v, u.v[c], acc.v[c]);
+        for (int c = 0; c < ChunkT<R>::K; ++c) d.v[c] = fma(a, x.v[c], y.v[c]);
+    }
+    return d;
+}
+
+template <class R>
+__device__ __forceinline__ ChunkT<R> scale_chunk(R a, const ChunkT<R>& x) {
+    ChunkT<R> d;
+#pragma unroll
+    for (int c = 0; c < ChunkT<R>::K; ++c) d.v[c] = a * x.v[c];
+    return d;
+}
+
+template <class R>
+__device__ __forceinline__ ChunkT<R> neg_chunk(const ChunkT<R>& x) {
+    ChunkT<R> d;
+#pragma unroll
+    for (int c = 0; c < ChunkT<R>::K; ++c) d.v[c] = -x.v[c];
+    return d;
+}
+
+template <class R, bool CPLX>
+__device__ __forceinline__ typename ValT<R, CPLX>::type shfl_val(
+    const typename ValT<R, CPLX>::type& v, int src, int width) {
+    if constexpr (CPLX) {
+        typename ValT<R, CPLX>::type o;
+        o.x = __shfl_sync(0xffffffffu, v.x, src, width);
+        o.y = __shfl_sync(0xffffffffu, v.y, src, width);
+        return o;
+    } else {
+        return __shfl_sync(0xffffffffu, v, src, width);
     }
 }
 
@@ -99,36 +201,24 @@ struct SellView {
 
 constexpr int STEP_THREADS = 256;
 
-template <class R, bool CPLX>
-__device__ __forceinline__ typename ValT<R, CPLX>::type shfl_val(
-    const typename ValT<R, CPLX>::type& v, int src, int width) {
-    if constexpr (CPLX) {
-        typename ValT<R, CPLX>::type o;
-        o.x = __shfl_sync(0xffffffffu, v.x, src, width);
-        o.y = __shfl_sync(0xffffffffu, v.y, src, width);
-        return o;
-    } else {
-        return __shfl_sync(0xffffffffu, v, src, width);
-    }
-}
-
-// Entries of one row handled per batch: all gathers of a batch are issued
-// back to back (one memory latency per batch instead of one per entry).
+// Entries of one row handled per batch on the generic (variable-width) path.
 template <int CPT>
 struct Batch {
     static constexpr int EB = CPT == 1 ? 16 : 8;
 };
 
-template <class R, bool CPLX, int G, int CPT, int MODE>
-__global__ void __launch_bounds__(STEP_THREADS, 2)
+// FW (full width): every thread's chunks lie inside the row (wc == G * CPT),
+// so no lane predicates are needed; inactive rows then read row 0 harmlessly.
+template <class R, bool CPLX, int G, int CPT, int MODE, int L, bool FW>
+__global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
     cheb_step_kernel(SellView H, StepArgs a, int wc) {
     using V = typename ValT<R, CPLX>::type;
     using Chunk = ChunkT<R>;
     constexpr int K = Chunk::K;
     constexpr int CPC = CPLX ? K / 2 : K;  // vector columns per chunk
     constexpr int SLOTS = STEP_THREADS / G;
-    constexpr int EB = Batch<CPT>::EB;
-    constexpr int EPL = (EB + G - 1) / G;  // entries loaded per lane per batch
+    constexpr int EB = L > 0 ? L : Batch<CPT>::EB;  // entries per batch
+    constexpr int EPL = (EB + G - 1) / G;           // entries loaded per lane per batch
     constexpr unsigned FULL = 0xffffffffu;
 
     const V* __restrict__ val = reinterpret_cast<const V*>(H.val);
@@ -154,75 +244,142 @@ __global__ void __launch_bounds__(STEP_THREADS, 2)
 #pragma unroll
         for (int c = 0; c < CPC; ++c) dot_a[q][c] = dot_b[q][c] = (R)0;
 
-    const int64_t nslots = (int64_t)gridDim.x * SLOTS;
-    // Warp-uniform loop: every lane runs the same iterations so the shuffles
-    // below always see the full warp; groups past the last row are inactive.
-    for (int64_t r = (int64_t)blockIdx.x * SLOTS + slot; __any_sync(FULL, r < H.n); r += nslots) {
-        const bool active = r < H.n;
-        int64_t base = 0, orig = 0;
-        int len = 0;
-        if (active) {
-            const int64_t k = r / H.C;
-            base = __ldg(H.chunk_ptr + k) + (r - k * H.C);
-            len = __ldg(H.chunk_len + k);
-            orig = H.perm ? __ldg(H.perm + r) : r;
+    // Row order: all blocks sweep the matrix as one front.  In wave w, block b
+    // takes the `tile` consecutive row groups starting at (w*grid + b)*tile*SLOTS,
+    // so a row's far neighbours (lattice +-z) are read by other SMs within one
+    // or two waves and stay in L2, while neighbours inside the tile hit in L1.
+    // The trip count is block-uniform, so every lane runs every iteration and
+    // the shuffles see the full warp.
+    const int tile = a.tile > 0 ? a.tile : 1;
+    const int64_t wave_rows = (int64_t)gridDim.x * tile * SLOTS;
+    const int iters = (int)((H.n + wave_rows - 1) / wave_rows) * tile;
+    const int64_t r_end = H.n;
+    auto row_of = [&](int it) -> int64_t {
+        const int64_t w = it / tile, t = it - w * tile;
+        return (w * gridDim.x + blockIdx.x) * (int64_t)tile * SLOTS + t * SLOTS + slot;
+    };
+
+    // Fixed-width path: the next row's entries are prefetched into (nc, nv).
+    int32_t nc[EPL];
+    V nv[EPL];
+    auto load_entries = [&](int64_t rr) {
+        const bool act = rr < r_end;
+        const int64_t k = rr / H.C;
+        const int64_t base = k * (int64_t)H.C * L + (rr - k * H.C);
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+            const int j = lane + e * G;
+            if (act && j < L) {
+                const int64_t pos = base + (int64_t)j * H.C;
+                nc[e] = __ldcs(colp + pos);
+                nv[e] = __ldcs(val + pos);
+            } else {
+                nc[e] = 0;
+                nv[e] = V{};
+            }
         }
+    };
+    if constexpr (L > 0) load_entries(row_of(0));
+
+    for (int it = 0; it < iters; ++it) {
+        const int64_t r = row_of(it);
+        const bool active = r < r_end;
+        const int64_t orig = active ? (H.perm ? __ldg(H.perm + r) : r) : 0;
+
         // own-row streams, issued before the gathers so their latency overlaps
-        Chunk uo[CPT], xo[CPT];
+        Chunk uo[CPT], xo[CPT], yo[CPT];
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
             const int ci = lane + q * G;
-            const bool on = active && ci < wc;
+            const bool on = FW || (active && ci < wc);
             const int64_t cofs = (int64_t)ci * K;
             if (on) uo[q] = load_chunk_ldg(u + orig * ldg + cofs);
             if (MODE == MODE_SECOND && on) xo[q] = load_chunk_cs(y + orig * ldy + cofs);
-            if (MODE == MODE_STEP && on) xo[q] = load_chunk_cs(w + orig * ldw + cofs);
+            if (MODE == MODE_STEP && on) {
+                xo[q] = load_chunk_cs(w + orig * ldw + cofs);
+                yo[q] = load_chunk_cs(y + orig * ldy + cofs);
+            }
         }
 
-        Chunk acc[CPT];
+        Acc<R, CPLX> acc[CPT];
 #pragma unroll
-        for (int q = 0; q < CPT; ++q)
-#pragma unroll
-            for (int c = 0; c < K; ++c) acc[q].v[c] = (R)0;
+        for (int q = 0; q < CPT; ++q) acc[q].zero();
 
-        const int maxlen = __reduce_max_sync(FULL, len);
-        for (int j0 = 0; j0 < maxlen; j0 += EB) {
-            // the group's lanes load the batch's column indices and values together
+        if constexpr (L > 0) {
             int32_t mc[EPL];
             V mv[EPL];
 #pragma unroll
             for (int e = 0; e < EPL; ++e) {
-                const int j = j0 + lane + e * G;
-                if (j < len) {
-                    const int64_t pos = base + (int64_t)j * H.C;
-                    mc[e] = __ldcs(colp + pos);
-                    mv[e] = __ldcs(val + pos);
-                } else {
-                    mc[e] = (int32_t)orig;
-                    mv[e] = V{};
-                }
+                mc[e] = nc[e];
+                mv[e] = nv[e];
             }
-            // issue every gather of the batch, then accumulate
-            Chunk g[EB][CPT];
+            // gathers of this row
+            Chunk g[L][CPT];
 #pragma unroll
-            for (int e = 0; e < EB; ++e) {
+            for (int e = 0; e < L; ++e) {
                 const int cj = __shfl_sync(FULL, mc[e / G], e % G, G);
                 const R* urow = u + (int64_t)cj * ldg;
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
                     const int ci = lane + q * G;
-                    if (j0 + e < len && ci < wc)
+                    if (FW || (active && ci < wc))
                         g[e][q] = load_chunk_ldg(urow + (int64_t)ci * K);
                     else
-#pragma unroll
-                        for (int c = 0; c < K; ++c) g[e][q].v[c] = (R)0;
+                        zero_chunk(g[e][q]);
                 }
             }
+            // prefetch the next row's entries while the gathers are in flight
+            load_entries(row_of(it + 1));
 #pragma unroll
-            for (int e = 0; e < EB; ++e) {
+            for (int e = 0; e < L; ++e) {
                 const V vj = shfl_val<R, CPLX>(mv[e / G], e % G, G);
 #pragma unroll
-                for (int q = 0; q < CPT; ++q) mac<R, CPLX>(acc[q], vj, g[e][q]);
+                for (int q = 0; q < CPT; ++q) acc[q].mac(vj, g[e][q]);
+            }
+        } else {
+            int64_t base = 0;
+            int len = 0;
+            if (active) {
+                const int64_t k = r / H.C;
+                base = __ldg(H.chunk_ptr + k) + (r - k * H.C);
+                len = __ldg(H.chunk_len + k);
+            }
+            const int maxlen = __reduce_max_sync(FULL, len);
+            for (int j0 = 0; j0 < maxlen; j0 += EB) {
+                int32_t mc[EPL];
+                V mv[EPL];
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) {
+                    const int j = j0 + lane + e * G;
+                    if (j < len) {
+                        const int64_t pos = base + (int64_t)j * H.C;
+                        mc[e] = __ldcs(colp + pos);
+                        mv[e] = __ldcs(val + pos);
+                    } else {
+                        mc[e] = 0;
+                        mv[e] = V{};
+                    }
+                }
+                Chunk g[EB][CPT];
+#pragma unroll
+                for (int e = 0; e < EB; ++e) {
+                    const int cj = __shfl_sync(FULL, mc[e / G], e % G, G);
+                    const R* urow = u + (int64_t)cj * ldg;
+#pragma unroll
+                    for (int q = 0; q < CPT; ++q) {
+                        const int ci = lane + q * G;
+                        if (j0 + e < len && ci < wc)
+                            g[e][q] = load_chunk_ldg(urow + (int64_t)ci * K);
+                        else
+                            zero_chunk(g[e][q]);
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < EB; ++e) {
+                    const V vj = shfl_val<R, CPLX>(mv[e / G], e % G, G);
+#pragma unroll
+                    for (int q = 0; q < CPT; ++q) acc[q].mac(vj, g[e][q]);
+                }
             }
         }
 
@@ -233,28 +390,21 @@ __global__ void __launch_bounds__(STEP_THREADS, 2)
             const int64_t cofs = (int64_t)ci * K;
             R* wp = w + orig * ldw + cofs;
             R* yp = y + orig * ldy + cofs;
+            const Chunk hu = acc[q].value();  // (H u)_i
             Chunk wn;
             if (MODE == MODE_SPMV) {
-#pragma unroll
-                for (int c = 0; c < K; ++c) wn.v[c] = fma(alpha, acc[q].v[c], beta * uo[q].v[c]);
+                wn = axpy_chunk(alpha, hu, scale_chunk(beta, uo[q]));
                 store_chunk_cs(wp, wn);
             } else if (MODE == MODE_SECOND) {
-                Chunk yn;
-#pragma unroll
-                for (int c = 0; c < K; ++c) {
-                    wn.v[c] = fma(two_alpha, acc[q].v[c], fma(two_beta, uo[q].v[c], -xo[q].v[c]));
-                    yn.v[c] = fma(c2, wn.v[c], fma(c1, uo[q].v[c], c0 * xo[q].v[c]));
-                }
+                // w = 2 alpha Hu + (2 beta u - x) ; y = c2 w + (c1 u + c0 x)
+                wn = axpy_chunk(two_alpha, hu, axpy_chunk(two_beta, uo[q], neg_chunk(xo[q])));
+                const Chunk yn =
+                    axpy_chunk(c2, wn, axpy_chunk(c1, uo[q], scale_chunk(c0, xo[q])));
                 store_chunk_cs(wp, wn);
                 store_chunk_cs(yp, yn);
             } else {
-                const Chunk yo = load_chunk_cs(yp);
-                Chunk yn;
-#pragma unroll
-                for (int c = 0; c < K; ++c) {
-                    wn.v[c] = fma(two_alpha, acc[q].v[c], fma(two_beta, uo[q].v[c], -xo[q].v[c]));
-                    yn.v[c] = fma(c0, wn.v[c], yo.v[c]);
-                }
+                wn = axpy_chunk(two_alpha, hu, axpy_chunk(two_beta, uo[q], neg_chunk(xo[q])));
+                const Chunk yn = axpy_chunk(c0, wn, yo[q]);
                 store_chunk_cs(wp, wn);
                 store_chunk_cs(yp, yn);
             }
@@ -264,7 +414,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 2)
                     if constexpr (CPLX) {
                         const R ur = uo[q].v[2 * c], ui = uo[q].v[2 * c + 1];
                         dot_a[q][c] = fma(ur, ur, fma(ui, ui, dot_a[q][c]));
-                        dot_b[q][c] = fma(ur, wn.v[2 * c], fma(ui, wn.v[2 * c + 1], dot_b[q][c]));
+                        dot_b[q][c] =
+                            fma(ur, wn.v[2 * c], fma(ui, wn.v[2 * c + 1], dot_b[q][c]));
                     } else {
                         dot_a[q][c] = fma(uo[q].v[c], uo[q].v[c], dot_a[q][c]);
                         dot_b[q][c] = fma(uo[q].v[c], wn.v[c], dot_b[q][c]);

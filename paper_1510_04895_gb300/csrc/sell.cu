@@ -359,6 +359,8 @@ void build_sell_from_device_csr(Matrix& M, const int64_t* rowptr, const int32_t*
     M.nnz_padded = total;
     M.nnz = nnz;
     M.max_row_len = maxlen;
+    // every chunk has the widest row's width exactly when the slot count says so
+    M.uniform_width = (total == M.nchunks * (int64_t)C * maxlen) ? maxlen : 0;
     const size_t vsz = M.complex_values ? 16 : 8;
     CHEBFD_CHECK_CUDA(cudaMalloc(&M.col, std::max<int64_t>(total, 1) * sizeof(int32_t)));
     CHEBFD_CHECK_CUDA(cudaMalloc(&M.val64, std::max<int64_t>(total, 1) * vsz));
