@@ -290,6 +290,59 @@ chebfd_status chebfd_convert_block(const void* X, chebfd_dtype xdt, int64_t ldx,
                                    chebfd_dtype ydt, int64_t ldy, int64_t n, int nb,
                                    void* stream);
 
+/* --------------------------------------------- batched ensembles (the benchmark spec) */
+
+/* Ensembles of independent matrices (e.g. disorder realisations of uneven
+ * size) filtered together.  The paper filters one matrix; batching many is
+ * the same filter (Fig. ChebFD) applied to a block-diagonal matrix.  Members
+ * must be built with sell_C = 1, sell_sigma = 1, share one constant row width
+ * (13 insulator, 4 graphene) and have dimensions divisible by sell_C; the
+ * ensemble stores its own copy (SELL chunk height sell_C), so the members
+ * may be destroyed afterwards.  Rows of member i are [off_i, off_{i+1}) of
+ * the ensemble; a search block for the ensemble is one row-major
+ * N_total x nb device block.  Synchronizes. */
+typedef struct chebfd_ensemble chebfd_ensemble;
+
+chebfd_status chebfd_ensemble_create(const chebfd_matrix* const* Hs, int count, int sell_C,
+                                     void* stream, chebfd_ensemble** out);
+
+/* n_total, count, row_offsets[count+1] (HOST, may be NULL), SELL chunk
+ * height, panel width and row tile of the launches (0 = defaults). */
+chebfd_status chebfd_ensemble_info(const chebfd_ensemble* E, int64_t* n_total, int* count,
+                                   int64_t* row_offsets, int* sell_C, int* panel, int* tile);
+
+/* Per-member filter coefficients: alpha[count], beta[count] (Eq. W1 for each
+ * member's own [a_i, b_i]) and gc[count * (Np+1)] (member i's g_n c_n at
+ * gc[i*(Np+1) + n]); all HOST arrays, copied to the device.  Synchronizes. */
+chebfd_status chebfd_ensemble_set_coeffs(chebfd_ensemble* E, const double* alpha,
+                                         const double* beta, const double* gc, int Np,
+                                         void* stream);
+
+/* Launch shape: panel width (columns per fused-step launch) and row tile
+ * (consecutive row groups per thread block and wave); 0 = defaults. */
+chebfd_status chebfd_ensemble_set_launch(chebfd_ensemble* E, int panel, int tile);
+
+/* X <- p_i[H_i] X on every member's rows at once (Fig. ChebFD with the
+ * members' own alpha, beta, g_n c_n): one fused launch per Chebyshev step
+ * covers all members.  use_graph != 0 captures the N_p launches once per
+ * (X, ld, nb, dtype, N_p, launch shape) into a CUDA graph (instantiated on
+ * the first call) and replays it: the whole ensemble filter is one graph
+ * launch.  Work vectors are owned by the ensemble.  Asynchronous. */
+chebfd_status chebfd_ensemble_filter(chebfd_ensemble* E, void* X, int64_t ld, int nb,
+                                     chebfd_dtype vdt, int use_graph, void* stream);
+
+/* Autotuner: builds the ensemble with SELL chunk heights 1, 2, 4 (those
+ * dividing every member dimension), times 7 Chebyshev steps on X for each
+ * panel width in {16, 32, 48, 64, 128} (admissible for vdt and <= nb) and row
+ * tile in {1, 4, 16}, and returns the fastest ensemble with its launch shape
+ * set; best_ms (HOST, may be NULL) receives the time per Chebyshev step.  X
+ * (N_total x nb, ld) is overwritten.  Synchronizes. */
+chebfd_status chebfd_ensemble_autotune(const chebfd_matrix* const* Hs, int count, void* X,
+                                       int64_t ld, int nb, chebfd_dtype vdt, void* stream,
+                                       chebfd_ensemble** out, double* best_ms);
+
+chebfd_status chebfd_ensemble_destroy(chebfd_ensemble* E);
+
 /* ------------------------------------------------------------- solve (A10) */
 
 typedef enum chebfd_precision {

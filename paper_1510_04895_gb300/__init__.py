@@ -9,4 +9,5 @@ from ._lib import (  # noqa: F401
     chebfd_filter_block, chebfd_kpm_moments, chebfd_matrix_create_csr,
     chebfd_matrix_create_lattice, chebfd_orthonormalize, chebfd_random_block,
     chebfd_rayleigh_ritz, chebfd_residuals, chebfd_scale_bounds, chebfd_solve, chebfd_spmv,
-    chebfd_window_coeffs, lib)
+    chebfd_window_coeffs, lib, Ensemble, chebfd_ensemble_create, chebfd_ensemble_autotune,
+    chebfd_filter_block_noalloc)

@@ -89,6 +89,18 @@ SIGNATURES = {
     "chebfd_result_get": (ctypes.c_int, [c_vp, c_vp]),
     "chebfd_result_destroy": (ctypes.c_int, [c_vp]),
     "chebfd_result_copy_vectors": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int64, c_vp]),
+    "chebfd_ensemble_create": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_int,
+                                              c_vp, ctypes.POINTER(c_vp)]),
+    "chebfd_ensemble_info": (ctypes.c_int, [c_vp, c_i64p, c_i32p, c_i64p, c_i32p, c_i32p,
+                                            c_i32p]),
+    "chebfd_ensemble_set_coeffs": (ctypes.c_int, [c_vp, c_dp, c_dp, c_dp, ctypes.c_int, c_vp]),
+    "chebfd_ensemble_set_launch": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int]),
+    "chebfd_ensemble_filter": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int64, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_int, c_vp]),
+    "chebfd_ensemble_autotune": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, c_vp,
+                                                ctypes.c_int64, ctypes.c_int, ctypes.c_int, c_vp,
+                                                ctypes.POINTER(c_vp), c_dp]),
+    "chebfd_ensemble_destroy": (ctypes.c_int, [c_vp]),
 }
 
 
@@ -364,6 +376,76 @@ def chebfd_solve(H, lam_lo, lam_hi, ns, Np, eps=1e-9, kernel="lanczos", mu=2.0, 
     finally:
         lib().chebfd_result_destroy(h)
     return out
+
+
+class Ensemble:
+    """Owner of a chebfd_ensemble handle (block-diagonal ensemble of matrices)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self._refresh()
+
+    def _refresh(self):
+        n = ctypes.c_int64()
+        cnt = ctypes.c_int32()
+        C, panel, tile = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().chebfd_ensemble_info(self.handle, ctypes.byref(n), ctypes.byref(cnt), None,
+                                          ctypes.byref(C), ctypes.byref(panel),
+                                          ctypes.byref(tile)), "chebfd_ensemble_info")
+        offs = np.zeros(cnt.value + 1, np.int64)
+        _check(lib().chebfd_ensemble_info(self.handle, None, None, offs.ctypes.data_as(c_i64p),
+                                          None, None, None), "chebfd_ensemble_info")
+        self.n, self.count, self.offsets = n.value, cnt.value, offs
+        self.sell_C, self.panel, self.tile = C.value, panel.value, tile.value
+
+    def set_coeffs(self, alpha, beta, gc, stream=None):
+        alpha = np.ascontiguousarray(alpha, np.float64)
+        beta = np.ascontiguousarray(beta, np.float64)
+        gc = np.ascontiguousarray(gc, np.float64)
+        Np = gc.shape[1] - 1
+        _check(lib().chebfd_ensemble_set_coeffs(self.handle, alpha.ctypes.data_as(c_dp),
+                                                beta.ctypes.data_as(c_dp), gc.ctypes.data_as(c_dp),
+                                                Np, _stream(stream)), "chebfd_ensemble_set_coeffs")
+
+    def set_launch(self, panel=0, tile=0):
+        _check(lib().chebfd_ensemble_set_launch(self.handle, panel, tile),
+               "chebfd_ensemble_set_launch")
+        self._refresh()
+
+    def filter(self, X, use_graph=True, stream=None):
+        _check(lib().chebfd_ensemble_filter(self.handle, _ptr(X), X.stride(0), X.shape[1],
+                                            dtype_of(X), 1 if use_graph else 0, _stream(stream)),
+               "chebfd_ensemble_filter")
+
+    def close(self):
+        if self.handle:
+            _check(lib().chebfd_ensemble_destroy(self.handle), "chebfd_ensemble_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def chebfd_ensemble_create(matrices, sell_C=1, stream=None):
+    arr = (c_vp * len(matrices))(*[m.handle for m in matrices])
+    h = c_vp()
+    _check(lib().chebfd_ensemble_create(arr, len(matrices), sell_C, _stream(stream),
+                                        ctypes.byref(h)), "chebfd_ensemble_create")
+    return Ensemble(h)
+
+
+def chebfd_ensemble_autotune(matrices, X, stream=None):
+    """Returns (ensemble with the fastest layout and launch shape, ms per step)."""
+    arr = (c_vp * len(matrices))(*[m.handle for m in matrices])
+    h = c_vp()
+    ms = ctypes.c_double()
+    _check(lib().chebfd_ensemble_autotune(arr, len(matrices), _ptr(X), X.stride(0), X.shape[1],
+                                          dtype_of(X), _stream(stream), ctypes.byref(h),
+                                          ctypes.byref(ms)), "chebfd_ensemble_autotune")
+    return Ensemble(h), ms.value
 
 
 def chebfd_random_block(X, col0=0, ns_total=None, seed=0, stream=None):

@@ -119,6 +119,12 @@ struct StepArgs {
     int64_t mom_ld;
     int mom_step;        // n of the step: writes mu_{2n-2}, mu_{2n-1} (SPMV: mu_0, mu_1)
     int tile;            // consecutive row groups per block and wave (0 = 1)
+    // Ensemble of independent matrices (block-diagonal): per-instance
+    // coefficients coef[inst * coef_ld + {0: alpha, 1: beta, 2 + n: gc_n}],
+    // instance of each (original) row in row_inst.  nullptr: single matrix.
+    const double* coef;
+    const int32_t* row_inst;
+    int coef_ld;
 };
 
 // Launch one step kernel.  dt selects the vector type, `single` the matrix copy.

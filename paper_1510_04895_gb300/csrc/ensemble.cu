@@ -1,0 +1,464 @@
+// Ensembles of independent matrices (disorder realisations) filtered together.
+//
+// The instances are stored as one block-diagonal SELL matrix (instance i owns
+// rows [off_i, off_i + N_i) and their columns), the search blocks of all
+// instances as one row-major block with the same n_b.  One launch of the
+// fused Chebyshev step then advances every instance by one step; each row
+// reads its instance's alpha, beta and g_n c_n from a small coefficient table.
+// The N_p launches of a filter are captured once into a CUDA graph and
+// replayed, so a whole ensemble filter is one graph launch.  A host-side
+// autotuner picks the SELL chunk height, the panel width and the row tile by
+// timing a few steps of each candidate.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+
+namespace chebfd {
+
+int max_panel_width(chebfd_dtype dt);
+void validate_block(const Matrix& M, chebfd_dtype dt, const void* X, int64_t ld, int nb);
+
+namespace {
+
+int grid_for(int64_t work) {
+    return (int)std::min<int64_t>(std::max<int64_t>((work + 255) / 256, 1), 16384);
+}
+
+// Copy instance rows into the ensemble layout (uniform width L, chunk height C).
+template <bool CPLX>
+__global__ void ens_fill_uniform(const int32_t* col, const double* v64, const float* v32,
+                                 int64_t n_i, int L, int64_t row_off, int C, int32_t* dcol,
+                                 double* d64, float* d32) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_i * L;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / L;
+        const int j = (int)(t - r * L);
+        const int64_t R = row_off + r;
+        const int64_t k = R / C;
+        const int64_t dst = k * (int64_t)C * L + (int64_t)j * C + (R - k * C);
+        const int64_t src = r * L + j;  // source chunk height 1
+        dcol[dst] = col[src] + (int32_t)row_off;
+        if (CPLX) {
+            d64[2 * dst] = v64[2 * src];
+            d64[2 * dst + 1] = v64[2 * src + 1];
+            if (v32) {
+                d32[2 * dst] = v32[2 * src];
+                d32[2 * dst + 1] = v32[2 * src + 1];
+            }
+        } else {
+            d64[dst] = v64[src];
+            if (v32) d32[dst] = v32[src];
+        }
+    }
+}
+
+__global__ void ens_chunk_uniform(int64_t nchunks, int C, int L, int64_t* chunk_ptr,
+                                  int32_t* chunk_len) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= nchunks;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        chunk_ptr[k] = k * (int64_t)C * L;
+        if (k < nchunks) chunk_len[k] = L;
+    }
+}
+
+__global__ void fill_int_kernel(int32_t* p, int64_t n, int32_t v) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x)
+        p[t] = v;
+}
+
+}  // namespace
+
+}  // namespace chebfd
+
+struct chebfd_ensemble {
+    chebfd::Matrix m;                 // block-diagonal SELL (owned arrays)
+    int count = 0;
+    std::vector<int64_t> offsets;     // count + 1 row offsets
+    int32_t* row_inst = nullptr;      // instance of each row
+    double* coef = nullptr;           // [count][Np + 3]
+    int Np = 0;
+    int panel = 0, tile = 0;          // tuned launch shape (0 = defaults)
+    void* work = nullptr;             // U and W work vectors
+    size_t work_bytes = 0;
+    std::map<std::tuple<void*, int64_t, int, int, int, int, int>, cudaGraphExec_t> graphs;
+};
+
+namespace chebfd {
+
+namespace {
+
+void free_ensemble(chebfd_ensemble* E) {
+    for (auto& kv : E->graphs) cudaGraphExecDestroy(kv.second);
+    E->graphs.clear();
+    cudaFree(E->m.chunk_ptr);
+    cudaFree(E->m.chunk_len);
+    cudaFree(E->m.col);
+    cudaFree(E->m.val64);
+    cudaFree(E->m.val32);
+    cudaFree(E->row_inst);
+    cudaFree(E->coef);
+    cudaFree(E->work);
+}
+
+void ensemble_build(chebfd_ensemble* E, const chebfd_matrix* const* Hs, int count, int C,
+                    cudaStream_t s) {
+    CHEBFD_REQUIRE(Hs && count >= 1, CHEBFD_EINVAL, "need at least one matrix");
+    CHEBFD_REQUIRE(C >= 1 && C <= 32 && (C & (C - 1)) == 0, CHEBFD_EINVAL,
+                   "chunk height must be a power of two in [1, 32]");
+    const Matrix& M0 = Hs[0]->m;
+    const bool cplx = M0.complex_values;
+    bool single = true;
+    const int L = M0.uniform_width;
+    int64_t n = 0;
+    E->offsets.assign(1, 0);
+    for (int i = 0; i < count; ++i) {
+        CHEBFD_REQUIRE(Hs[i] != nullptr, CHEBFD_EINVAL, "null matrix in ensemble");
+        const Matrix& Mi = Hs[i]->m;
+        CHEBFD_REQUIRE(Mi.complex_values == cplx, CHEBFD_EINVAL,
+                       "ensemble members must all be complex or all real");
+        CHEBFD_REQUIRE(Mi.C == 1 && Mi.identity_perm, CHEBFD_EINVAL,
+                       "ensemble members must be built with sell_C = 1, sell_sigma = 1");
+        CHEBFD_REQUIRE(L > 0 && Mi.uniform_width == L, CHEBFD_EUNSUPPORTED,
+                       "ensemble members must share one constant row width");
+        CHEBFD_REQUIRE(Mi.n % C == 0, CHEBFD_EINVAL,
+                       "every member dimension must be a multiple of the chunk height");
+        single = single && Mi.val32 != nullptr;
+        n += Mi.n;
+        E->offsets.push_back(n);
+    }
+    CHEBFD_REQUIRE(n < (1LL << 31), CHEBFD_EINVAL, "ensemble dimension must be < 2^31");
+    Matrix& M = E->m;
+    M = Matrix{};
+    M.n = n;
+    M.complex_values = cplx;
+    M.identity_perm = true;
+    M.C = C;
+    M.sigma = 1;
+    M.nchunks = n / C;
+    M.max_row_len = L;
+    M.uniform_width = L;
+    M.nnz = n * L;
+    M.nnz_padded = n * L;
+    M.device = M0.device;
+    M.num_sms = M0.num_sms;
+    const size_t vs = cplx ? 16 : 8;
+    CHEBFD_CHECK_CUDA(cudaMalloc(&M.chunk_ptr, (M.nchunks + 1) * sizeof(int64_t)));
+    CHEBFD_CHECK_CUDA(cudaMalloc(&M.chunk_len, M.nchunks * sizeof(int32_t)));
+    CHEBFD_CHECK_CUDA(cudaMalloc(&M.col, M.nnz_padded * sizeof(int32_t)));
+    CHEBFD_CHECK_CUDA(cudaMalloc(&M.val64, M.nnz_padded * vs));
+    if (single) CHEBFD_CHECK_CUDA(cudaMalloc(&M.val32, M.nnz_padded * vs / 2));
+    CHEBFD_CHECK_CUDA(cudaMalloc(&E->row_inst, n * sizeof(int32_t)));
+    ens_chunk_uniform<<<grid_for(M.nchunks + 1), 256, 0, s>>>(M.nchunks, C, L, M.chunk_ptr,
+                                                              M.chunk_len);
+    for (int i = 0; i < count; ++i) {
+        const Matrix& Mi = Hs[i]->m;
+        const int64_t off = E->offsets[i];
+        if (cplx)
+            ens_fill_uniform<true><<<grid_for(Mi.n * L), 256, 0, s>>>(
+                Mi.col, (const double*)Mi.val64, single ? (const float*)Mi.val32 : nullptr, Mi.n,
+                L, off, C, M.col, (double*)M.val64, (float*)M.val32);
+        else
+            ens_fill_uniform<false><<<grid_for(Mi.n * L), 256, 0, s>>>(
+                Mi.col, (const double*)Mi.val64, single ? (const float*)Mi.val32 : nullptr, Mi.n,
+                L, off, C, M.col, (double*)M.val64, (float*)M.val32);
+        fill_int_kernel<<<grid_for(Mi.n), 256, 0, s>>>(E->row_inst + off, Mi.n, i);
+    }
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+    CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    E->count = count;
+}
+
+void set_coeffs(chebfd_ensemble* E, const double* alpha, const double* beta, const double* gc,
+                int Np, cudaStream_t s) {
+    CHEBFD_REQUIRE(alpha && beta && gc && Np >= 2, CHEBFD_EINVAL, "bad coefficient arguments");
+    const int ldc = Np + 3;
+    std::vector<double> h((size_t)E->count * ldc);
+    for (int i = 0; i < E->count; ++i) {
+        h[(size_t)i * ldc] = alpha[i];
+        h[(size_t)i * ldc + 1] = beta[i];
+        for (int n = 0; n <= Np; ++n) h[(size_t)i * ldc + 2 + n] = gc[(size_t)i * (Np + 1) + n];
+    }
+    if (Np != E->Np) {
+        for (auto& kv : E->graphs) cudaGraphExecDestroy(kv.second);
+        E->graphs.clear();
+        cudaFree(E->coef);
+        E->coef = nullptr;
+        CHEBFD_CHECK_CUDA(cudaMalloc(&E->coef, h.size() * sizeof(double)));
+        E->Np = Np;
+    }
+    CHEBFD_CHECK_CUDA(
+        cudaMemcpyAsync(E->coef, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+int64_t padded_cols(chebfd_dtype dt, int nb) {
+    const int64_t per = (int64_t)(16 / dtype_size(dt));
+    return ((nb + per - 1) / per) * per;
+}
+
+// Queue the whole ensemble filter (all panels, all N_p steps) on stream s.
+void queue_filter(chebfd_ensemble* E, void* X, int64_t ld, int nb, chebfd_dtype dt,
+                  cudaStream_t s) {
+    const Matrix& M = E->m;
+    const int pw = E->panel > 0 ? std::min(E->panel, max_panel_width(dt)) : max_panel_width(dt);
+    const int wmax = std::min(pw, nb);
+    const int64_t ldw = padded_cols(dt, wmax);
+    const size_t es = dtype_size(dt);
+    char* U = (char*)E->work;
+    char* W = U + (size_t)M.n * ldw * es;
+    const int Np = E->Np;
+    for (int p0 = 0; p0 < nb; p0 += pw) {
+        const int pnb = std::min(pw, nb - p0);
+        CHEBFD_REQUIRE(((size_t)pnb * es) % 16 == 0, CHEBFD_EINVAL,
+                       "panel width * element size must be a multiple of 16 bytes");
+        char* Xp = (char*)X + p0 * es;
+        StepArgs a{};
+        a.nb = pnb;
+        a.tile = E->tile;
+        a.coef = E->coef;
+        a.row_inst = E->row_inst;
+        a.coef_ld = Np + 3;
+        a.gather = Xp;
+        a.ldg = ld;
+        a.w = U;
+        a.ldw = ldw;
+        a.mom_step = 1;
+        launch_step(M, dt, MODE_SPMV, a, s);
+        a.gather = U;
+        a.ldg = ldw;
+        a.w = W;
+        a.y = Xp;
+        a.ldy = ld;
+        a.mom_step = 2;
+        launch_step(M, dt, MODE_SECOND, a, s);
+        char* u = U;
+        char* w = W;
+        for (int n = 3; n <= Np; ++n) {
+            std::swap(u, w);
+            a.gather = u;
+            a.w = w;
+            a.mom_step = n;
+            launch_step(M, dt, MODE_STEP, a, s);
+        }
+    }
+}
+
+void ensure_work(chebfd_ensemble* E, int nb, chebfd_dtype dt) {
+    const int pw = E->panel > 0 ? std::min(E->panel, max_panel_width(dt)) : max_panel_width(dt);
+    const size_t need = 2 * (size_t)E->m.n * padded_cols(dt, std::min(pw, nb)) * dtype_size(dt);
+    if (need <= E->work_bytes) return;
+    for (auto& kv : E->graphs) cudaGraphExecDestroy(kv.second);
+    E->graphs.clear();
+    cudaFree(E->work);
+    E->work = nullptr;
+    E->work_bytes = 0;
+    CHEBFD_CHECK_CUDA(cudaMalloc(&E->work, need));
+    E->work_bytes = need;
+}
+
+void ensemble_filter(chebfd_ensemble* E, void* X, int64_t ld, int nb, chebfd_dtype dt,
+                     bool use_graph, cudaStream_t s) {
+    validate_block(E->m, dt, X, ld, nb);
+    CHEBFD_REQUIRE(E->coef != nullptr, CHEBFD_EINVAL, "set the ensemble coefficients first");
+    ensure_work(E, nb, dt);
+    if (!use_graph) {
+        queue_filter(E, X, ld, nb, dt, s);
+        return;
+    }
+    const auto key = std::make_tuple(X, ld, nb, (int)dt, E->Np, E->panel, E->tile);
+    auto it = E->graphs.find(key);
+    if (it == E->graphs.end()) {
+        cudaStream_t cs;
+        CHEBFD_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        CHEBFD_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        try {
+            queue_filter(E, X, ld, nb, dt, cs);
+        } catch (...) {
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            throw;
+        }
+        CHEBFD_CHECK_CUDA(cudaStreamEndCapture(cs, &g));
+        cudaStreamDestroy(cs);
+        const cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        CHEBFD_CHECK_CUDA(e);
+        it = E->graphs.emplace(key, ge).first;
+    }
+    CHEBFD_CHECK_CUDA(cudaGraphLaunch(it->second, s));
+}
+
+double time_steps(chebfd_ensemble* E, void* X, int64_t ld, int nb, chebfd_dtype dt,
+                  cudaStream_t s) {
+    cudaEvent_t e0, e1;
+    CHEBFD_CHECK_CUDA(cudaEventCreate(&e0));
+    CHEBFD_CHECK_CUDA(cudaEventCreate(&e1));
+    ensemble_filter(E, X, ld, nb, dt, false, s);  // warm-up
+    CHEBFD_CHECK_CUDA(cudaEventRecord(e0, s));
+    ensemble_filter(E, X, ld, nb, dt, false, s);
+    CHEBFD_CHECK_CUDA(cudaEventRecord(e1, s));
+    CHEBFD_CHECK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+}  // namespace
+
+}  // namespace chebfd
+
+using namespace chebfd;
+
+extern "C" {
+
+chebfd_status chebfd_ensemble_create(const chebfd_matrix* const* Hs, int count, int sell_C,
+                                     void* stream, chebfd_ensemble** out) {
+    chebfd_ensemble* E = nullptr;
+    chebfd_status st = guarded([&] {
+        CHEBFD_REQUIRE(out, CHEBFD_EINVAL, "null output");
+        E = new chebfd_ensemble();
+        ensemble_build(E, Hs, count, sell_C, as_stream(stream));
+    });
+    if (st != CHEBFD_OK) {
+        if (E) {
+            free_ensemble(E);
+            delete E;
+        }
+        return st;
+    }
+    *out = E;
+    return CHEBFD_OK;
+}
+
+chebfd_status chebfd_ensemble_info(const chebfd_ensemble* E, int64_t* n_total, int* count,
+                                   int64_t* row_offsets, int* sell_C, int* panel, int* tile) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(E, CHEBFD_EINVAL, "null ensemble");
+        if (n_total) *n_total = E->m.n;
+        if (count) *count = E->count;
+        if (row_offsets) std::copy(E->offsets.begin(), E->offsets.end(), row_offsets);
+        if (sell_C) *sell_C = E->m.C;
+        if (panel) *panel = E->panel;
+        if (tile) *tile = E->tile;
+    });
+}
+
+chebfd_status chebfd_ensemble_set_coeffs(chebfd_ensemble* E, const double* alpha,
+                                         const double* beta, const double* gc, int Np,
+                                         void* stream) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(E, CHEBFD_EINVAL, "null ensemble");
+        set_coeffs(E, alpha, beta, gc, Np, as_stream(stream));
+    });
+}
+
+chebfd_status chebfd_ensemble_set_launch(chebfd_ensemble* E, int panel, int tile) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(E && panel >= 0 && tile >= 0, CHEBFD_EINVAL, "bad launch shape");
+        E->panel = panel;
+        E->tile = tile;
+    });
+}
+
+chebfd_status chebfd_ensemble_filter(chebfd_ensemble* E, void* X, int64_t ld, int nb,
+                                     chebfd_dtype vdt, int use_graph, void* stream) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(E, CHEBFD_EINVAL, "null ensemble");
+        ensemble_filter(E, X, ld, nb, vdt, use_graph != 0, as_stream(stream));
+    });
+}
+
+chebfd_status chebfd_ensemble_autotune(const chebfd_matrix* const* Hs, int count, void* X,
+                                       int64_t ld, int nb, chebfd_dtype vdt, void* stream,
+                                       chebfd_ensemble** out, double* best_ms) {
+    chebfd_ensemble* best = nullptr;
+    chebfd_status st = guarded([&] {
+        CHEBFD_REQUIRE(out && X, CHEBFD_EINVAL, "null argument");
+        cudaStream_t s = as_stream(stream);
+        // candidate shapes: SELL chunk height C, panel width, row tile
+        const int Cs[] = {1, 2, 4};
+        const int tiles[] = {1, 4, 16};
+        std::vector<int> panels;
+        for (int p : {16, 32, 48, 64, 128})
+            if (p <= max_panel_width(vdt) && ((size_t)p * dtype_size(vdt)) % 16 == 0 && p <= nb)
+                panels.push_back(p);
+        if (panels.empty()) panels.push_back(std::min(nb, max_panel_width(vdt)));
+        std::vector<double> al(count, 0.1), be(count, 0.0), gc((size_t)count * 8, 0.0);
+        double best_t = 1e30;
+        int best_panel = 0, best_tile = 0;
+        for (int C : Cs) {
+            bool ok = true;
+            for (int i = 0; i < count; ++i) ok = ok && Hs[i] && Hs[i]->m.n % C == 0;
+            if (!ok) continue;
+            auto* E = new chebfd_ensemble();
+            try {
+                ensemble_build(E, Hs, count, C, s);
+                set_coeffs(E, al.data(), be.data(), gc.data(), 7, s);
+                for (int p : panels)
+                    for (int t : tiles) {
+                        E->panel = p;
+                        E->tile = t;
+                        const double ms = time_steps(E, X, ld, nb, vdt, s);
+                        if (ms < best_t) {
+                            best_t = ms;
+                            best_panel = p;
+                            best_tile = t;
+                            if (best != E) {
+                                if (best) {
+                                    free_ensemble(best);
+                                    delete best;
+                                }
+                                best = E;
+                            }
+                        }
+                    }
+            } catch (...) {
+                if (E != best) {
+                    free_ensemble(E);
+                    delete E;
+                }
+                throw;
+            }
+            if (E != best) {
+                free_ensemble(E);
+                delete E;
+            }
+        }
+        CHEBFD_REQUIRE(best != nullptr, CHEBFD_EINVAL, "no admissible ensemble layout");
+        best->panel = best_panel;
+        best->tile = best_tile;
+        for (auto& kv : best->graphs) cudaGraphExecDestroy(kv.second);
+        best->graphs.clear();
+        if (best_ms) *best_ms = best_t / 7.0;  // per Chebyshev step (7 launches per panel set)
+    });
+    if (st != CHEBFD_OK) {
+        if (best) {
+            free_ensemble(best);
+            delete best;
+        }
+        return st;
+    }
+    *out = best;
+    return CHEBFD_OK;
+}
+
+chebfd_status chebfd_ensemble_destroy(chebfd_ensemble* E) {
+    return guarded([&] {
+        if (!E) return;
+        free_ensemble(E);
+        delete E;
+    });
+}
+
+}  // extern "C"

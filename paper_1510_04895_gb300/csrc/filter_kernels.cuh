@@ -286,6 +286,25 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
         const bool active = r < r_end;
         const int64_t orig = active ? (H.perm ? __ldg(H.perm + r) : r) : 0;
 
+        // ensemble: this row's instance coefficients (tiny table, L1-resident)
+        R alpha_r = alpha, beta_r = beta, two_alpha_r = two_alpha, two_beta_r = two_beta;
+        R c0r = c0, c1r = c1, c2r = c2;
+        if (a.coef != nullptr && active) {
+            const double* cf = a.coef + (int64_t)__ldg(a.row_inst + orig) * a.coef_ld;
+            const double al = __ldg(cf), be = __ldg(cf + 1);
+            alpha_r = (R)al;
+            beta_r = (R)be;
+            two_alpha_r = (R)(2.0 * al);
+            two_beta_r = (R)(2.0 * be);
+            if (MODE == MODE_SECOND) {
+                c0r = (R)__ldg(cf + 2);
+                c1r = (R)__ldg(cf + 3);
+                c2r = (R)__ldg(cf + 4);
+            } else if (MODE == MODE_STEP) {
+                c0r = (R)__ldg(cf + 2 + a.mom_step);
+            }
+        }
+
         // own-row streams, issued before the gathers so their latency overlaps
         Chunk uo[CPT], xo[CPT], yo[CPT];
 #pragma unroll
@@ -393,18 +412,20 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
             const Chunk hu = acc[q].value();  // (H u)_i
             Chunk wn;
             if (MODE == MODE_SPMV) {
-                wn = axpy_chunk(alpha, hu, scale_chunk(beta, uo[q]));
+                wn = axpy_chunk(alpha_r, hu, scale_chunk(beta_r, uo[q]));
                 store_chunk_cs(wp, wn);
             } else if (MODE == MODE_SECOND) {
                 // w = 2 alpha Hu + (2 beta u - x) ; y = c2 w + (c1 u + c0 x)
-                wn = axpy_chunk(two_alpha, hu, axpy_chunk(two_beta, uo[q], neg_chunk(xo[q])));
+                wn = axpy_chunk(two_alpha_r, hu,
+                                axpy_chunk(two_beta_r, uo[q], neg_chunk(xo[q])));
                 const Chunk yn =
-                    axpy_chunk(c2, wn, axpy_chunk(c1, uo[q], scale_chunk(c0, xo[q])));
+                    axpy_chunk(c2r, wn, axpy_chunk(c1r, uo[q], scale_chunk(c0r, xo[q])));
                 store_chunk_cs(wp, wn);
                 store_chunk_cs(yp, yn);
             } else {
-                wn = axpy_chunk(two_alpha, hu, axpy_chunk(two_beta, uo[q], neg_chunk(xo[q])));
-                const Chunk yn = axpy_chunk(c0, wn, yo[q]);
+                wn = axpy_chunk(two_alpha_r, hu,
+                                axpy_chunk(two_beta_r, uo[q], neg_chunk(xo[q])));
+                const Chunk yn = axpy_chunk(c0r, wn, yo[q]);
                 store_chunk_cs(wp, wn);
                 store_chunk_cs(yp, yn);
             }

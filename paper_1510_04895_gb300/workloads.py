@@ -33,3 +33,22 @@ def random_block(seed, n, nb, complex_values, dtype=None):
     if complex_values:
         X = X + 1j * rs.uniform(-1.0, 1.0, (n, nb))
     return X.astype(dtype) if dtype is not None else X
+
+
+# Disorder ensemble: 512 insulators, member i has seed 100 + i, lattice edge
+# L_i uniform in {10..20} (N = 4 L^3 between 4000 and 32000) and disorder W_i
+# uniform in [0.2, 2.0], both drawn from numpy's PCG64 seeded with 100 + i;
+# window [-0.05, 0.05], n_s = 48, N_p = 300, Lanczos kernel (mu = 2).
+ENSEMBLE = dict(count=512, first_seed=100, window=(-0.05, 0.05), ns=48, Np=300, t=1.0, m=1.0,
+                kernel="lanczos")
+
+
+def ensemble_members(count=512, first_seed=100):
+    """[(L, W, seed)] of the disorder ensemble."""
+    out = []
+    for i in range(count):
+        rs = np.random.default_rng(first_seed + i)
+        L = int(rs.integers(10, 21))
+        W = float(rs.uniform(0.2, 2.0))
+        out.append((L, W, first_seed + i))
+    return out
