@@ -263,6 +263,40 @@ def bench_ensemble(pkg, workloads, dev, peak_gbs):
             "autotune_ms_per_step": ms_step_tune}
 
 
+def bench_solve(pkg, H, a, b, delta, Np, ns, eps=1e-9):
+    """Wall time of the whole ChebFD solve (Sec. 3.1 steps 4-8) to residual
+    <= eps ||H|| for every accepted pair in [-delta, delta]: plain FP64 against
+    the mixed form (complex64 filter until the residuals stall, then FP64
+    sweeps; FP64 Gram, Rayleigh-Ritz and residuals throughout)."""
+    import torch
+    out = {}
+    lams = {}
+    for prec in ("fp64", "mixed"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = pkg.chebfd_solve(H, -delta, delta, ns, Np, eps=eps, kernel="lanczos", precision=prec,
+                             a=a, b=b, max_iter=40, seed=0)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        normH = max(abs(r["a"]), abs(r["b"]))
+        lam = np.sort(r["lam"])
+        lams[prec] = lam
+        out[prec] = {"seconds": t, "iterations": r["iterations"],
+                     "fp64_filter_iterations": r["fp64_iterations"], "nev": r["nev"],
+                     "converged": r["converged"], "max_residual_over_normH":
+                         float(r["res"].max() / normH) if r["nev"] else None,
+                     "seconds_filter": r["seconds_filter"], "seconds_dense": r["seconds_dense"],
+                     "n_mvm": r["n_mvm"],
+                     "chiral_pairing_error": float(np.abs(lam + lam[::-1]).max()) if r["nev"] else None}
+    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    if len(lams["fp64"]) == len(lams["mixed"]) and len(lams["fp64"]):
+        out["max_eigenvalue_difference"] = float(np.abs(lams["fp64"] - lams["mixed"]).max())
+    out["eps"] = eps
+    out["workload"] = "topi 64x64x32x4, window [-%.6g, %.6g], n_s = %d, N_p = %d, Lanczos mu=2" % (
+        delta, delta, ns, Np)
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -377,6 +411,8 @@ def run_ours(args):
 
     if not args.no_ensemble:
         out["ensemble"] = bench_ensemble(pkg, workloads, dev, peaks["hbm_gbs"])
+    if not args.no_solve:
+        out["time_to_solution"] = bench_solve(pkg, H, a, b, delta, Np, w["ns"])
 
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, desc = oracle_sample(w, a, b, delta, args.cpu_steps)
@@ -403,6 +439,7 @@ def main():
     p.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=8)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-ensemble", action="store_true")
+    p.add_argument("--no-solve", action="store_true")
     args = p.parse_args()
     if args.impl == "reference":
         return run_reference(args)
