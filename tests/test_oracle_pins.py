@@ -404,3 +404,44 @@ def test_chebfd_small_topi_against_dense():
     assert np.abs(r["V"].conj().T @ r["V"] - np.eye(len(ew))).max() < 1e-12
     th = np.sort(r["theta"])
     assert np.abs(th + th[::-1]).max() < 1e-10           # chiral +- pairing
+
+
+# ---------------------------------------------------------------- MLP reference
+
+
+def test_mlp_gradient_matches_central_differences():
+    from oracle import mlp
+    rs = np.random.default_rng(0)
+    P = mlp.init_params(7, 5, 3, seed=1)
+    for k in P:
+        P[k] = P[k] + 0.1 * rs.standard_normal(P[k].shape)
+    X = rs.standard_normal((6, 7))
+    T = np.c_[rs.standard_normal((6, 2)), rs.integers(0, 2, 6)]
+    L0, G = mlp.loss_and_grad(P, X, T)
+    assert L0 == pytest.approx(mlp.loss(P, X, T), rel=1e-14)
+    h = 1e-6
+    for k in P:
+        flat = P[k].reshape(-1)
+        for idx in range(flat.size):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp = mlp.loss(P, X, T)
+            flat[idx] = old - h
+            lm = mlp.loss(P, X, T)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - G[k].reshape(-1)[idx]) <= 1e-6 * max(1.0, abs(fd)), (k, idx)
+
+
+def test_mlp_adam_reduces_loss_on_a_fittable_target():
+    from oracle import mlp
+    rs = np.random.default_rng(3)
+    X = rs.standard_normal((32, 4))
+    T = np.c_[X[:, 0] * 0.5, np.tanh(X[:, 1]), (X[:, 2] > 0).astype(float)]
+    P = mlp.init_params(4, 16, 3, seed=2)
+    st = {}
+    L_start = mlp.loss(P, X, T)
+    for _ in range(300):
+        _, G = mlp.loss_and_grad(P, X, T)
+        mlp.adam_step(P, G, st, 1e-2)
+    assert mlp.loss(P, X, T) < 0.2 * L_start
