@@ -343,6 +343,62 @@ chebfd_status chebfd_ensemble_autotune(const chebfd_matrix* const* Hs, int count
 
 chebfd_status chebfd_ensemble_destroy(chebfd_ensemble* E);
 
+/* ------------------------------------------- parameter choice (A13, learned) */
+
+/* Features of (H, window) for the parameter-predicting MLP: m_feat normalised
+ * KPM moments mu_0..mu_{m_feat-1} of alpha H + beta (1024 moments from 8
+ * probe vectors of SplitMix64 stream 2, Sec. 3.1 step 1), then the window
+ * centre alpha (lam_lo+lam_hi)/2 + beta, log10 of the scaled half width
+ * alpha (lam_hi-lam_lo)/2, and log10 max(N_T, 1) with N_T the KPM count of
+ * Eq. DOS:target.  [a, b] with b <= a is computed by chebfd_scale_bounds.
+ * features: HOST array of m_feat + 3 doubles; n_target (HOST, may be NULL)
+ * receives N_T.  Synchronizes. */
+chebfd_status chebfd_param_features(const chebfd_matrix* H, double a, double b, double lam_lo,
+                                    double lam_hi, int m_feat, uint64_t seed, double* features,
+                                    double* n_target, void* stream);
+
+typedef struct chebfd_mlp chebfd_mlp;
+
+/* (n_s, N_p, kernel) for the window.  mlp == NULL: the paper's rules - N_T
+ * from the KPM DOS (Eq. DOS:target), n_s = 4 N_T (Sec. 2.4, linear DOS;
+ * Sec. 3.1 step 2) rounded up to a multiple of 8 (>= 16), the margin delta'
+ * at which the KPM count reaches n_s (Eq. DOS:search), N_p = N_0 S_w/delta'
+ * (Eq. etafit) with N_0 of Tab. lanczoskernel at the window centre, Lanczos
+ * kernel.  Otherwise the MLP's outputs (log N_p, log n_s, kernel logit) on the
+ * features of chebfd_param_features (m_feat moments).  Results are HOST ints;
+ * kernel is a chebfd_kernel.  Synchronizes. */
+chebfd_status chebfd_choose_params(const chebfd_matrix* H, double a, double b, double lam_lo,
+                                   double lam_hi, chebfd_mlp* mlp, int m_feat, uint64_t seed,
+                                   int* ns, int* Np, int* kernel, double* n_target,
+                                   void* stream);
+
+/* --------------------------------------------------- MLP (K9, the benchmark spec) */
+
+/* Fully connected network x (n_in) -> tanh (n_hidden) -> tanh (n_hidden) ->
+ * 3 outputs (log N_p, log n_s, kernel logit), FP32 on the device, trained
+ * and evaluated by this library's kernels.  No counterpart in the paper; the
+ * nearest passage is the adaptive choice of N_p and N_S from the DOS
+ * suggested in Sec. 6.  Parameters are packed W1 (n_h x n_in, row-major), b1,
+ * W2 (n_h x n_h), b2, W3 (3 x n_h), b3; they start at zero. */
+chebfd_status chebfd_mlp_create(int n_in, int n_hidden, int n_out, chebfd_mlp** out);
+chebfd_status chebfd_mlp_num_params(const chebfd_mlp* N, int64_t* count);
+/* Copy packed parameters from HOST floats (resets the Adam state). */
+chebfd_status chebfd_mlp_set_params(chebfd_mlp* N, const float* host, int64_t count);
+/* Copy packed parameters and/or the last gradient to HOST floats (either may be NULL). */
+chebfd_status chebfd_mlp_get_params(const chebfd_mlp* N, float* host, float* host_grads,
+                                    int64_t count);
+/* Z (DEVICE, B x 3) = network(X (DEVICE, B x n_in, row-major)).  Asynchronous. */
+chebfd_status chebfd_mlp_forward(chebfd_mlp* N, const float* X, int B, float* Z, void* stream);
+/* Loss (1/B) sum_b [(z0-t0)^2 + (z1-t1)^2 + softplus(z2) - t2 z2] of targets
+ * T (DEVICE, B x 3, t2 in {0,1}) and its gradient, kept for chebfd_mlp_adam.
+ * loss (HOST, may be NULL; non-NULL synchronizes). */
+chebfd_status chebfd_mlp_loss_grad(chebfd_mlp* N, const float* X, const float* T, int B,
+                                   float* loss, void* stream);
+/* One Adam step (Kingma-Ba) with the last gradient. Asynchronous. */
+chebfd_status chebfd_mlp_adam(chebfd_mlp* N, float lr, float beta1, float beta2, float eps,
+                              void* stream);
+chebfd_status chebfd_mlp_destroy(chebfd_mlp* N);
+
 /* ------------------------------------------------------------- solve (A10) */
 
 typedef enum chebfd_precision {

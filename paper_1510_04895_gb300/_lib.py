@@ -101,7 +101,28 @@ SIGNATURES = {
                                                 ctypes.c_int64, ctypes.c_int, ctypes.c_int, c_vp,
                                                 ctypes.POINTER(c_vp), c_dp]),
     "chebfd_ensemble_destroy": (ctypes.c_int, [c_vp]),
+    "chebfd_param_features": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_uint64, c_dp, c_dp, c_vp]),
+    "chebfd_choose_params": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, c_vp, ctypes.c_int,
+                                            ctypes.c_uint64, c_i32p, c_i32p, c_i32p, c_dp, c_vp]),
+    "chebfd_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(c_vp)]),
+    "chebfd_mlp_num_params": (ctypes.c_int, [c_vp, c_i64p]),
+    "chebfd_mlp_set_params": (ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_float),
+                                             ctypes.c_int64]),
+    "chebfd_mlp_get_params": (ctypes.c_int, [c_vp, ctypes.POINTER(ctypes.c_float),
+                                             ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+    "chebfd_mlp_forward": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int, c_vp, c_vp]),
+    "chebfd_mlp_loss_grad": (ctypes.c_int, [c_vp, c_vp, c_vp, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_float), c_vp]),
+    "chebfd_mlp_adam": (ctypes.c_int, [c_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, c_vp]),
+    "chebfd_mlp_destroy": (ctypes.c_int, [c_vp]),
 }
+
+KERNEL_NAMES = {v: k for k, v in KERNEL_IDS.items()}
 
 
 class Params(ctypes.Structure):
@@ -446,6 +467,101 @@ def chebfd_ensemble_autotune(matrices, X, stream=None):
                                           dtype_of(X), _stream(stream), ctypes.byref(h),
                                           ctypes.byref(ms)), "chebfd_ensemble_autotune")
     return Ensemble(h), ms.value
+
+
+def chebfd_param_features(H, lam_lo, lam_hi, m_feat=64, a=0.0, b=0.0, seed=0, stream=None):
+    f = np.zeros(m_feat + 3)
+    nt = ctypes.c_double()
+    _check(lib().chebfd_param_features(H.handle, a, b, lam_lo, lam_hi, m_feat, seed,
+                                       f.ctypes.data_as(c_dp), ctypes.byref(nt), _stream(stream)),
+           "chebfd_param_features")
+    return f, nt.value
+
+
+def chebfd_choose_params(H, lam_lo, lam_hi, mlp=None, m_feat=64, a=0.0, b=0.0, seed=0,
+                         stream=None):
+    """(n_s, N_p, kernel name, N_T estimate) from the paper's rules or the MLP."""
+    ns, Np, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    nt = ctypes.c_double()
+    _check(lib().chebfd_choose_params(H.handle, a, b, lam_lo, lam_hi,
+                                      mlp.handle if mlp is not None else None, m_feat, seed,
+                                      ctypes.byref(ns), ctypes.byref(Np), ctypes.byref(k),
+                                      ctypes.byref(nt), _stream(stream)), "chebfd_choose_params")
+    return ns.value, Np.value, KERNEL_NAMES[k.value], nt.value
+
+
+class MLP:
+    """Device MLP (n_in -> n_h -> n_h -> 3) trained by the library's kernels."""
+
+    def __init__(self, n_in, n_hidden=128):
+        h = c_vp()
+        _check(lib().chebfd_mlp_create(n_in, n_hidden, 3, ctypes.byref(h)), "chebfd_mlp_create")
+        self.handle = h
+        self.n_in, self.n_hidden = n_in, n_hidden
+        c = ctypes.c_int64()
+        _check(lib().chebfd_mlp_num_params(h, ctypes.byref(c)), "chebfd_mlp_num_params")
+        self.count = c.value
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        assert flat.size == self.count
+        _check(lib().chebfd_mlp_set_params(self.handle, flat.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_float)), self.count), "chebfd_mlp_set_params")
+
+    def get_params(self):
+        p = np.zeros(self.count, np.float32)
+        g = np.zeros(self.count, np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(lib().chebfd_mlp_get_params(self.handle, p.ctypes.data_as(fp),
+                                           g.ctypes.data_as(fp), self.count),
+               "chebfd_mlp_get_params")
+        return p, g
+
+    def forward(self, X, stream=None):
+        import torch
+        Z = torch.empty((X.shape[0], 3), dtype=torch.float32, device=X.device)
+        _check(lib().chebfd_mlp_forward(self.handle, _ptr(X), X.shape[0], _ptr(Z),
+                                        _stream(stream)), "chebfd_mlp_forward")
+        return Z
+
+    def loss_grad(self, X, T, stream=None):
+        loss = ctypes.c_float()
+        _check(lib().chebfd_mlp_loss_grad(self.handle, _ptr(X), _ptr(T), X.shape[0],
+                                          ctypes.byref(loss), _stream(stream)),
+               "chebfd_mlp_loss_grad")
+        return loss.value
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        _check(lib().chebfd_mlp_adam(self.handle, lr, beta1, beta2, eps, _stream(stream)),
+               "chebfd_mlp_adam")
+
+    def close(self):
+        if self.handle:
+            _check(lib().chebfd_mlp_destroy(self.handle), "chebfd_mlp_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack_params(P):
+    """Packed parameter vector (W1, b1, W2, b2, W3, b3) of a dict of arrays."""
+    return np.concatenate([np.asarray(P[k], np.float64).reshape(-1)
+                           for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+
+def unpack_params(flat, n_in, n_h, n_out=3):
+    shapes = [("W1", (n_h, n_in)), ("b1", (n_h,)), ("W2", (n_h, n_h)), ("b2", (n_h,)),
+              ("W3", (n_out, n_h)), ("b3", (n_out,))]
+    out, o = {}, 0
+    for k, s in shapes:
+        n = int(np.prod(s))
+        out[k] = np.asarray(flat[o:o + n], np.float64).reshape(s)
+        o += n
+    return out
 
 
 def chebfd_random_block(X, col0=0, ns_total=None, seed=0, stream=None):
