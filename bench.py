@@ -288,6 +288,36 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, eps=1e-9):
                      "seconds_filter": r["seconds_filter"], "seconds_dense": r["seconds_dense"],
                      "n_mvm": r["n_mvm"],
                      "chiral_pairing_error": float(np.abs(lam + lam[::-1]).max()) if r["nev"] else None}
+    # learned parameters: (N_p, n_s, kernel) from the trained MLP on the KPM
+    # features of this matrix and window, with the mixed-precision solve
+    wpath = os.path.join(ROOT, "paper_1510_04895_gb300", "data", "mlp_weights.npy")
+    if os.path.exists(wpath):
+        from paper_1510_04895_gb300 import mlp_train
+        net = pkg.MLP(mlp_train.N_IN, 128)
+        net.set_params(np.load(wpath).astype(np.float32))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ns_m, Np_m, kern_m, nt = pkg.chebfd_choose_params(H, -delta, delta, mlp=net, a=a, b=b,
+                                                          m_feat=mlp_train.M_FEAT)
+        ns_m = max(ns_m, int(np.ceil(nt / 4.0)) * 4 + 8)   # never fewer vectors than targets
+        r = pkg.chebfd_solve(H, -delta, delta, ns_m, Np_m, eps=eps, kernel=kern_m,
+                             precision="mixed", a=a, b=b, max_iter=40, seed=0)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        normH = max(abs(r["a"]), abs(r["b"]))
+        lam = np.sort(r["lam"])
+        out["mixed_mlp"] = {"seconds": t, "ns": ns_m, "Np": Np_m, "kernel": kern_m,
+                            "kpm_n_target": nt, "iterations": r["iterations"],
+                            "fp64_filter_iterations": r["fp64_iterations"], "nev": r["nev"],
+                            "converged": r["converged"],
+                            "max_residual_over_normH": float(r["res"].max() / normH)
+                            if r["nev"] else None,
+                            "seconds_filter": r["seconds_filter"],
+                            "seconds_dense": r["seconds_dense"]}
+        if len(lam) == len(lams["fp64"]) and len(lam):
+            out["mixed_mlp"]["max_eigenvalue_difference_vs_fp64"] = float(
+                np.abs(lam - lams["fp64"]).max())
+        out["speedup_mixed_mlp_over_fp64"] = out["fp64"]["seconds"] / t
     out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
     if len(lams["fp64"]) == len(lams["mixed"]) and len(lams["fp64"]):
         out["max_eigenvalue_difference"] = float(np.abs(lams["fp64"] - lams["mixed"]).max())

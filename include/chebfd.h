@@ -469,6 +469,21 @@ chebfd_status chebfd_result_copy_vectors(const chebfd_result* r, void* dst, int6
 
 chebfd_status chebfd_result_destroy(chebfd_result* r);
 
+/* chebfd_solve for every member of an ensemble at once (one ensemble filter
+ * per iteration, one CUDA-graph launch; SVQB and Rayleigh-Ritz member by
+ * member on their row slices; the convergence and ghost rules of
+ * chebfd_solve per member).  Hs[count] are the member matrices the ensemble
+ * was built from (used for H V in the projection), a[count], b[count] their
+ * spectral intervals (HOST), p the common window, eps, ns, Np, kernel, mu,
+ * precision, max_iter and seed (p->a, p->b, p->nb, p->lanczos_steps
+ * ignored).  MIXED precision filters in single precision until every
+ * unconverged member has stalled, then in FP64.  outs[count] receive one
+ * result per member (converged or not; destroy each).  iterations (HOST, may
+ * be NULL) receives the iterations run.  Synchronizes. */
+chebfd_status chebfd_solve_batched(chebfd_ensemble* E, const chebfd_matrix* const* Hs,
+                                   const double* a, const double* b, const chebfd_params* p,
+                                   void* stream, chebfd_result** outs, int* iterations);
+
 #ifdef __cplusplus
 }
 #endif

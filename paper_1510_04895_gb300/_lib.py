@@ -120,6 +120,8 @@ SIGNATURES = {
     "chebfd_mlp_adam": (ctypes.c_int, [c_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, c_vp]),
     "chebfd_mlp_destroy": (ctypes.c_int, [c_vp]),
+    "chebfd_solve_batched": (ctypes.c_int, [c_vp, ctypes.POINTER(c_vp), c_dp, c_dp, c_vp, c_vp,
+                                            ctypes.POINTER(c_vp), c_i32p]),
 }
 
 KERNEL_NAMES = {v: k for k, v in KERNEL_IDS.items()}
@@ -467,6 +469,56 @@ def chebfd_ensemble_autotune(matrices, X, stream=None):
                                           dtype_of(X), _stream(stream), ctypes.byref(h),
                                           ctypes.byref(ms)), "chebfd_ensemble_autotune")
     return Ensemble(h), ms.value
+
+
+def _result_dict(h, n, is_complex, st=0, vectors=True):
+    import torch
+    info = ResultInfo()
+    _check(lib().chebfd_result_get(h, ctypes.byref(info)), "chebfd_result_get")
+    nev = info.nev
+    lam = np.ctypeslib.as_array(info.lambda_, (nev,)).copy() if nev else np.zeros(0)
+    res = np.ctypeslib.as_array(info.res, (nev,)).copy() if nev else np.zeros(0)
+    V = None
+    if vectors:
+        dt = torch.complex128 if is_complex else torch.float64
+        V = torch.empty((n, max(nev, 1)), dtype=dt, device="cuda")[:, :nev]
+        if nev:
+            _check(lib().chebfd_result_copy_vectors(h, _ptr(V), V.stride(0), _stream(None)),
+                   "chebfd_result_copy_vectors")
+    return dict(lam=lam, res=res, V=V, nev=nev, iterations=info.iterations,
+                converged=bool(info.converged), fp64_iterations=info.fp64_iterations,
+                n_mvm=info.n_mvm, a=info.a, b=info.b, seconds_filter=info.seconds_filter,
+                seconds_dense=info.seconds_dense, seconds_total=info.seconds_total,
+                status=STATUS[st])
+
+
+def chebfd_solve_batched(E, matrices, a, b, lam_lo, lam_hi, ns, Np, eps=1e-9, kernel="lanczos",
+                         mu=2.0, precision="fp64", max_iter=50, seed=0, vectors=False,
+                         stream=None):
+    """ChebFD on every ensemble member; returns (list of per-member dicts, iterations)."""
+    cnt = len(matrices)
+    arr = (c_vp * cnt)(*[m.handle for m in matrices])
+    a = np.ascontiguousarray(a, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    p = Params(lam_lo=lam_lo, lam_hi=lam_hi, eps=eps, a=0.0, b=0.0, mu=mu, ns=ns, Np=Np,
+               kernel=KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel), nb=0,
+               precision=1 if precision == "mixed" else 0, max_iter=max_iter, lanczos_steps=0,
+               reserved=0, seed=seed)
+    outs = (c_vp * cnt)()
+    its = ctypes.c_int32()
+    _check(lib().chebfd_solve_batched(E.handle, arr, a.ctypes.data_as(c_dp),
+                                      b.ctypes.data_as(c_dp), ctypes.byref(p), _stream(stream),
+                                      outs, ctypes.byref(its)), "chebfd_solve_batched")
+    results = []
+    try:
+        for i in range(cnt):
+            results.append(_result_dict(outs[i], matrices[i].n, matrices[i].is_complex,
+                                        vectors=vectors))
+    finally:
+        for i in range(cnt):
+            if outs[i]:
+                lib().chebfd_result_destroy(outs[i])
+    return results, its.value
 
 
 def chebfd_param_features(H, lam_lo, lam_hi, m_feat=64, a=0.0, b=0.0, seed=0, stream=None):

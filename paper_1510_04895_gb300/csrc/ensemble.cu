@@ -316,6 +316,167 @@ double time_steps(chebfd_ensemble* E, void* X, int64_t ld, int nb, chebfd_dtype 
 
 }  // namespace
 
+void orthonormalize_impl(void* Yv, int64_t n, int ns, int64_t ld, chebfd_dtype dt,
+                         uint64_t seed, int64_t* refill_counter, int* rank_out, cudaStream_t s);
+void rayleigh_ritz_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype dt,
+                        double* theta_host, double* res_host, void* HY_out, cudaStream_t s);
+void convert_block_impl(const void* X, chebfd_dtype xdt, int64_t ldx, void* Y, chebfd_dtype ydt,
+                        int64_t ldy, int64_t n, int nb, cudaStream_t s);
+void launch_random_block(void* X, int64_t n, int64_t ld, int nb, int col0, int ns_total,
+                         uint64_t seed, chebfd_dtype dt, cudaStream_t stream);
+void fill_result(chebfd_result* R, const std::vector<int>& acc, const std::vector<double>& theta,
+                 const std::vector<double>& res, const void* Y, int64_t n, int64_t ld,
+                 size_t es, int iterations, bool converged, int fp64_its, int64_t n_mvm,
+                 double a, double b, cudaStream_t s);
+chebfd_result* new_result();
+
+// The ChebFD iteration of Sec. 3.1 for every member of an ensemble at once:
+// one ensemble filter per iteration (all members, one graph launch), then
+// SVQB and Rayleigh-Ritz member by member on their row slices, with the
+// convergence and ghost test of chebfd_solve per member.  A converged
+// member's pairs are taken at that iteration; its rows keep being filtered
+// (the launch covers all rows) but are no longer projected.  MIXED precision
+// runs the ensemble filter in single precision until every unconverged
+// member has stalled above 1e-9 ||H_i|| (largest accepted residual falling
+// less than 2x), then in FP64.
+void solve_batched_impl(chebfd_ensemble* E, const chebfd_matrix* const* Hs, const double* av,
+                        const double* bv, const chebfd_params& p0, cudaStream_t s,
+                        chebfd_result** outs, int* iterations_out) {
+    chebfd_params p = p0;
+    CHEBFD_REQUIRE(p.ns >= 4 && p.ns <= 1024 && p.ns % 4 == 0, CHEBFD_EINVAL,
+                   "need 4 <= ns <= 1024, ns a multiple of 4");
+    CHEBFD_REQUIRE(p.Np >= 2 && p.lam_hi > p.lam_lo && p.eps > 0.0, CHEBFD_EINVAL,
+                   "bad solve parameters");
+    if (p.mu <= 0.0) p.mu = 2.0;
+    if (p.max_iter <= 0) p.max_iter = 50;
+    const int count = E->count;
+    const bool cplx = E->m.complex_values;
+    const chebfd_dtype d64 = cplx ? CHEBFD_C128 : CHEBFD_R64;
+    const chebfd_dtype d32 = cplx ? CHEBFD_C64 : CHEBFD_R32;
+    const bool mixed = p.precision == CHEBFD_PRECISION_MIXED;
+    CHEBFD_REQUIRE(!mixed || E->m.val32 != nullptr, CHEBFD_EINVAL,
+                   "mixed precision needs members built with also_single");
+    for (int i = 0; i < count; ++i) {
+        CHEBFD_REQUIRE(Hs[i] && Hs[i]->m.n == E->offsets[i + 1] - E->offsets[i], CHEBFD_EINVAL,
+                       "member matrices do not match the ensemble");
+        CHEBFD_REQUIRE(bv[i] > av[i], CHEBFD_EINVAL, "need b > a for every member");
+        outs[i] = nullptr;
+    }
+    // per-member coefficients of the common window
+    std::vector<double> al(count), be(count), gc((size_t)count * (p.Np + 1));
+    for (int i = 0; i < count; ++i) {
+        al[i] = 2.0 / (bv[i] - av[i]);
+        be[i] = (av[i] + bv[i]) / (av[i] - bv[i]);
+        const chebfd_status st = chebfd_window_coeffs(av[i], bv[i], p.lam_lo, p.lam_hi, p.Np,
+                                                      (chebfd_kernel)p.kernel, p.mu,
+                                                      gc.data() + (size_t)i * (p.Np + 1));
+        CHEBFD_REQUIRE(st == CHEBFD_OK, st, "coefficient construction failed");
+    }
+    set_coeffs(E, al.data(), be.data(), gc.data(), p.Np, s);
+    const int64_t n = E->m.n;
+    const int ns = p.ns;
+    const int64_t ld = ns;
+    void *Y64 = nullptr, *X32 = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(Y64);
+        cudaFree(X32);
+    };
+    try {
+        CHEBFD_CHECK_CUDA(cudaMalloc(&Y64, (size_t)n * ld * dtype_size(d64)));
+        if (mixed) CHEBFD_CHECK_CUDA(cudaMalloc(&X32, (size_t)n * ld * dtype_size(d32)));
+        launch_random_block(Y64, n, ld, ns, 0, ns, p.seed, d64, s);
+        bool single_phase = mixed;
+        if (mixed) convert_block_impl(Y64, d64, ld, X32, d32, ld, n, ns, s);
+        struct State {
+            bool done = false, stalled = false;
+            double prev_worst = -1.0;
+            std::vector<double> prev_theta, prev_res;
+            int64_t refill = 0;
+        };
+        std::vector<State> st(count);
+        std::vector<double> theta(ns), res(ns);
+        int it = 0, fp64_its = 0, remaining = count;
+        for (it = 1; it <= p.max_iter && remaining > 0; ++it) {
+            if (single_phase) {
+                ensemble_filter(E, X32, ld, ns, d32, true, s);
+                convert_block_impl(X32, d32, ld, Y64, d64, ld, n, ns, s);
+            } else {
+                ensemble_filter(E, Y64, ld, ns, d64, true, s);
+                ++fp64_its;
+            }
+            bool all_stalled = true;
+            for (int i = 0; i < count; ++i) {
+                State& S = st[i];
+                if (S.done) continue;
+                const Matrix& Mi = Hs[i]->m;
+                void* Yi = (char*)Y64 + (size_t)E->offsets[i] * ld * dtype_size(d64);
+                orthonormalize_impl(Yi, Mi.n, ns, ld, d64, p.seed + 1000003ULL * i, &S.refill,
+                                    nullptr, s);
+                rayleigh_ritz_impl(Mi, Yi, ld, ns, d64, theta.data(), res.data(), nullptr, s);
+                const double normH = std::max(std::fabs(av[i]), std::fabs(bv[i]));
+                std::vector<int> acc;
+                for (int k = 0; k < ns; ++k) {
+                    if (!(theta[k] >= p.lam_lo && theta[k] <= p.lam_hi)) continue;
+                    bool ghost = false;
+                    if (!S.prev_theta.empty()) {
+                        int j = 0;
+                        for (int q = 1; q < ns; ++q)
+                            if (std::fabs(S.prev_theta[q] - theta[k]) <
+                                std::fabs(S.prev_theta[j] - theta[k]))
+                                j = q;
+                        ghost = res[k] > std::sqrt(p.eps) * normH &&
+                                !(S.prev_res[j] >= 10.0 * res[k]);
+                    }
+                    if (!ghost) acc.push_back(k);
+                }
+                double worst = 0.0;
+                for (int k : acc) worst = std::max(worst, res[k]);
+                const bool conv = !acc.empty() && worst <= p.eps * normH;
+                if (conv && !single_phase) {
+                    outs[i] = new_result();
+                    fill_result(outs[i], acc, theta, res, Yi, Mi.n, ld, dtype_size(d64), it, true,
+                                fp64_its, (int64_t)it * ns * p.Np, av[i], bv[i], s);
+                    S.done = true;
+                    --remaining;
+                    continue;
+                }
+                if (single_phase) {
+                    S.stalled = S.stalled || conv ||
+                                (S.prev_worst > 0.0 && worst > 1e-9 * normH &&
+                                 worst > 0.5 * S.prev_worst);
+                    all_stalled = all_stalled && S.stalled;
+                }
+                S.prev_worst = worst;
+                S.prev_theta = theta;
+                S.prev_res = res;
+                if (it == p.max_iter) {
+                    outs[i] = new_result();
+                    fill_result(outs[i], acc, theta, res, Yi, Mi.n, ld, dtype_size(d64), it,
+                                false, fp64_its, (int64_t)it * ns * p.Np, av[i], bv[i], s);
+                }
+            }
+            if (single_phase && all_stalled) single_phase = false;
+            if (single_phase) convert_block_impl(Y64, d64, ld, X32, d32, ld, n, ns, s);
+        }
+        for (int i = 0; i < count; ++i)
+            if (!outs[i]) {  // iteration budget ended before this member was visited
+                outs[i] = new_result();
+                fill_result(outs[i], {}, theta, res, Y64, Hs[i]->m.n, ld, dtype_size(d64), it,
+                            false, fp64_its, (int64_t)it * ns * p.Np, av[i], bv[i], s);
+            }
+        if (iterations_out) *iterations_out = std::min(it, p.max_iter);
+    } catch (...) {
+        cleanup();
+        for (int i = 0; i < count; ++i)
+            if (outs[i]) {
+                chebfd_result_destroy(outs[i]);
+                outs[i] = nullptr;
+            }
+        throw;
+    }
+    cleanup();
+}
+
 }  // namespace chebfd
 
 using namespace chebfd;
@@ -451,6 +612,15 @@ chebfd_status chebfd_ensemble_autotune(const chebfd_matrix* const* Hs, int count
     }
     *out = best;
     return CHEBFD_OK;
+}
+
+chebfd_status chebfd_solve_batched(chebfd_ensemble* E, const chebfd_matrix* const* Hs,
+                                   const double* a, const double* b, const chebfd_params* p,
+                                   void* stream, chebfd_result** outs, int* iterations) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(E && Hs && a && b && p && outs, CHEBFD_EINVAL, "null argument");
+        solve_batched_impl(E, Hs, a, b, *p, as_stream(stream), outs, iterations);
+    });
 }
 
 chebfd_status chebfd_ensemble_destroy(chebfd_ensemble* E) {

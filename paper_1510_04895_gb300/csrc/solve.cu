@@ -26,6 +26,15 @@ int max_panel_width(chebfd_dtype dt);
 
 }  // namespace chebfd
 
+struct chebfd_result;
+
+namespace chebfd {
+void fill_result(chebfd_result* R, const std::vector<int>& acc, const std::vector<double>& theta,
+                 const std::vector<double>& res, const void* Y, int64_t n, int64_t ld,
+                 size_t es, int iterations, bool converged, int fp64_its, int64_t n_mvm,
+                 double a, double b, cudaStream_t s);
+}  // namespace chebfd
+
 struct chebfd_result {
     chebfd_result_info info{};
     std::vector<double> lambda, res;
@@ -155,35 +164,45 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
     }
     if (it > p.max_iter) it = p.max_iter;
     // ---- collect the accepted pairs (ascending theta: already sorted)
-    const int nev = (int)acc_idx.size();
+    fill_result(R, acc_idx, theta, res, Y64.p, n, ld, dtype_size(d64), it, converged, fp64_its,
+                (int64_t)it * ns * p.Np, a, b, s);
+    R->info.seconds_filter = t_filter;
+    R->info.seconds_dense = t_dense;
+    R->info.seconds_total = now() - t_start;
+}
+
+chebfd_result* new_result() { return new chebfd_result(); }
+
+// Copy the accepted Ritz pairs (columns acc of the row-major block Y) into R.
+void fill_result(chebfd_result* R, const std::vector<int>& acc, const std::vector<double>& theta,
+                 const std::vector<double>& res, const void* Y, int64_t n, int64_t ld,
+                 size_t es, int iterations, bool converged, int fp64_its, int64_t n_mvm,
+                 double a, double b, cudaStream_t s) {
+    const int nev = (int)acc.size();
     R->lambda.resize(nev);
     R->res.resize(nev);
-    const size_t es = dtype_size(d64);
     R->n = n;
     R->elem_size = es;
     if (nev > 0) {
         CHEBFD_CHECK_CUDA(cudaMalloc(&R->V, (size_t)n * nev * es));
         for (int q = 0; q < nev; ++q) {
-            const int k = acc_idx[q];
+            const int k = acc[q];
             R->lambda[q] = theta[k];
             R->res[q] = res[k];
             CHEBFD_CHECK_CUDA(cudaMemcpy2DAsync((char*)R->V + q * es, nev * es,
-                                                (char*)Y64.p + k * es, ld * es, es, n,
+                                                (const char*)Y + k * es, ld * es, es, n,
                                                 cudaMemcpyDeviceToDevice, s));
         }
         CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
     }
     chebfd_result_info& I = R->info;
     I.nev = nev;
-    I.iterations = it;
+    I.iterations = iterations;
     I.converged = converged ? 1 : 0;
     I.fp64_iterations = fp64_its;
-    I.n_mvm = (int64_t)it * ns * p.Np;
+    I.n_mvm = n_mvm;
     I.a = a;
     I.b = b;
-    I.seconds_filter = t_filter;
-    I.seconds_dense = t_dense;
-    I.seconds_total = now() - t_start;
     I.lambda = R->lambda.data();
     I.res = R->res.data();
     I.V = R->V;

@@ -114,3 +114,33 @@ def test_ensemble_rejects_mismatched_members():
     s = pkg.chebfd_matrix_create_lattice("topi", 3, 3, 3, W=0.5, seed=1, sell_C=4)
     with pytest.raises(pkg.ChebFDError):
         pkg.chebfd_ensemble_create([a, s])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_solve_matches_dense_per_member(precision):
+    """chebfd_solve_batched on a 5-member ensemble: every member's window
+    eigenvalues equal the dense eigensolver's within 1e-10 ||H||, residuals
+    <= 1e-9 ||H||."""
+    members = [(4, 0.4, 100), (5, 1.7, 101), (4, 0.9, 102), (6, 2.0, 103), (5, 0.2, 104)]
+    mats, a, b = [], [], []
+    for L, W, seed in members:
+        mats.append(pkg.chebfd_matrix_create_lattice("topi", L, L, L, t=1.0, m=1.0, W=W,
+                                                     seed=seed, also_single=True))
+        bound = 1.01 * (1.0 + 3.0 + W / 2)
+        a.append(-bound)
+        b.append(bound)
+    E = pkg.chebfd_ensemble_create(mats, sell_C=1)
+    res, its = pkg.chebfd_solve_batched(E, mats, a, b, -0.3, 0.3, 32, 160, eps=1e-9,
+                                        precision=precision, max_iter=40, vectors=True)
+    assert its >= 1
+    for i, (L, W, seed) in enumerate(members):
+        e = np.linalg.eigvalsh(lattice.to_scipy(*lattice.topi_csr(L, L, L, t=1.0, m=1.0, W=W,
+                                                                  seed=seed)).toarray())
+        exact = np.sort(e[np.abs(e) <= 0.3])
+        r = res[i]
+        normH = max(abs(a[i]), abs(b[i]))
+        assert r["converged"] and r["nev"] == len(exact), (i, r["nev"], len(exact))
+        assert np.abs(np.sort(r["lam"]) - exact).max() <= 1e-10 * normH
+        assert r["res"].max() <= 1e-9 * normH
+        V = r["V"].cpu().numpy()
+        assert np.abs(V.conj().T @ V - np.eye(r["nev"])).max() <= 1e-12
