@@ -434,7 +434,9 @@ typedef struct chebfd_result chebfd_result;
  * whose residual exceeds sqrt(eps) ||H|| and did not fall by >= 10x against
  * the previous iteration's pair nearest in theta is discarded.  Converged
  * when at least one pair is accepted and every accepted in-window pair has
- * residual <= eps ||H||; the restart block is the set of Ritz vectors.
+ * residual <= eps ||H||, or (empty window) when two successive iterations
+ * from the second on accept no pair; the restart block is the set of Ritz
+ * vectors.
  * MIXED precision switches to FP64 filter sweeps once the largest accepted
  * residual exceeds 1e-9 ||H|| and fell by less than 2x in an iteration.
  * Result handle owned by the library (chebfd_result_destroy).  ENOCONV when

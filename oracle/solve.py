@@ -9,7 +9,11 @@ Readings of the paper taken here (the paper leaves them open):
   against the residual of the previous iteration's pair nearest in theta;
 * convergence (step 8a): at least one accepted in-window pair, and every
   accepted in-window pair below eps ||H||; the window is closed,
-  lam_lo <= theta <= lam_hi;
+  lam_lo <= theta <= lam_hi.  Step 8a holds vacuously for a window without
+  eigenvalues; such a window is taken as empty once two successive
+  iterations (from the second on, when ghosts are recognised) accept no
+  in-window pair - a true eigenpair's residual falls by the filter's damping
+  factor per iteration, so it would have been accepted;
 * restart (step 8b): the next search block is the full set of Ritz vectors,
   which spans the same space as the orthonormalised filtered block;
 * search vectors (step 4): SplitMix64 stream 1, column k of n_s, entry 2u-1 at
@@ -45,6 +49,7 @@ def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
     refill = 0
     log = []
     prev = None
+    prev_empty = False
     result = None
     for it in range(1, max_iter + 1):
         Y = filter_fn(X) if filter_fn is not None else filt.filter_block(H, alpha, beta, gc, X)
@@ -60,6 +65,10 @@ def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
                     ghost[k] = True
         acc = inwin & ~ghost
         converged = bool(acc.any()) and bool(np.all(res[acc] <= eps * normH))
+        empty_now = prev is not None and not acc.any()
+        if empty_now and prev_empty:
+            converged = True
+        prev_empty = empty_now
         log.append(dict(iteration=it, rank=rank, in_window=int(inwin.sum()),
                         ghosts=int(ghost.sum()), accepted=int(acc.sum()),
                         res_min=float(res[acc].min()) if acc.any() else None,

@@ -388,7 +388,7 @@ void solve_batched_impl(chebfd_ensemble* E, const chebfd_matrix* const* Hs, cons
         bool single_phase = mixed;
         if (mixed) convert_block_impl(Y64, d64, ld, X32, d32, ld, n, ns, s);
         struct State {
-            bool done = false, stalled = false;
+            bool done = false, stalled = false, prev_empty = false;
             double prev_worst = -1.0;
             std::vector<double> prev_theta, prev_res;
             int64_t refill = 0;
@@ -431,8 +431,12 @@ void solve_batched_impl(chebfd_ensemble* E, const chebfd_matrix* const* Hs, cons
                 }
                 double worst = 0.0;
                 for (int k : acc) worst = std::max(worst, res[k]);
-                const bool conv = !acc.empty() && worst <= p.eps * normH;
-                if (conv && !single_phase) {
+                bool conv = !acc.empty() && worst <= p.eps * normH;
+                // empty window: two successive iterations (ghosts recognised) accept nothing
+                const bool empty_now = !S.prev_theta.empty() && acc.empty();
+                const bool empty = empty_now && S.prev_empty;
+                S.prev_empty = empty_now;
+                if (empty || (conv && !single_phase)) {
                     outs[i] = new_result();
                     fill_result(outs[i], acc, theta, res, Yi, Mi.n, ld, dtype_size(d64), it, true,
                                 fp64_its, (int64_t)it * ns * p.Np, av[i], bv[i], s);

@@ -207,9 +207,10 @@ struct Batch {
     static constexpr int EB = CPT == 1 ? 16 : 8;
 };
 
-// FW (full width): every thread's chunks lie inside the row (wc == G * CPT),
-// so no lane predicates are needed; inactive rows then read row 0 harmlessly.
-template <class R, bool CPLX, int G, int CPT, int MODE, int L, bool FW>
+// ENS: rows of an ensemble read their member's alpha, beta and g_n c_n from a
+// coefficient table (a separate instantiation, so the single-matrix kernel
+// carries none of that code).
+template <class R, bool CPLX, int G, int CPT, int MODE, int L, bool ENS>
 __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
     cheb_step_kernel(SellView H, StepArgs a, int wc) {
     using V = typename ValT<R, CPLX>::type;
@@ -233,9 +234,10 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
     constexpr int RPE = CPLX ? 2 : 1;  // reals per vector element
     const int64_t ldg = a.ldg * RPE, ldw = a.ldw * RPE, ldy = a.ldy * RPE;
 
-    const R alpha = (R)a.alpha, beta = (R)a.beta;
-    const R two_alpha = (R)(2.0 * a.alpha), two_beta = (R)(2.0 * a.beta);
-    const R c0 = (R)a.c0, c1 = (R)a.c1, c2 = (R)a.c2;
+    // per-launch scalars (an ensemble row overwrites them with its member's)
+    R alpha = (R)a.alpha, beta = (R)a.beta;
+    R two_alpha = (R)(2.0 * a.alpha), two_beta = (R)(2.0 * a.beta);
+    R c0 = (R)a.c0, c1 = (R)a.c1, c2 = (R)a.c2;
 
     R dot_a[CPT][CPC];
     R dot_b[CPT][CPC];
@@ -286,22 +288,22 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
         const bool active = r < r_end;
         const int64_t orig = active ? (H.perm ? __ldg(H.perm + r) : r) : 0;
 
-        // ensemble: this row's instance coefficients (tiny table, L1-resident)
-        R alpha_r = alpha, beta_r = beta, two_alpha_r = two_alpha, two_beta_r = two_beta;
-        R c0r = c0, c1r = c1, c2r = c2;
-        if (a.coef != nullptr && active) {
-            const double* cf = a.coef + (int64_t)__ldg(a.row_inst + orig) * a.coef_ld;
-            const double al = __ldg(cf), be = __ldg(cf + 1);
-            alpha_r = (R)al;
-            beta_r = (R)be;
-            two_alpha_r = (R)(2.0 * al);
-            two_beta_r = (R)(2.0 * be);
-            if (MODE == MODE_SECOND) {
-                c0r = (R)__ldg(cf + 2);
-                c1r = (R)__ldg(cf + 3);
-                c2r = (R)__ldg(cf + 4);
-            } else if (MODE == MODE_STEP) {
-                c0r = (R)__ldg(cf + 2 + a.mom_step);
+        // ensemble: this row's member coefficients (tiny table, L1-resident)
+        if constexpr (ENS) {
+            if (active) {
+                const double* cf = a.coef + (int64_t)__ldg(a.row_inst + orig) * a.coef_ld;
+                const double al = __ldg(cf), be = __ldg(cf + 1);
+                alpha = (R)al;
+                beta = (R)be;
+                two_alpha = (R)(2.0 * al);
+                two_beta = (R)(2.0 * be);
+                if (MODE == MODE_SECOND) {
+                    c0 = (R)__ldg(cf + 2);
+                    c1 = (R)__ldg(cf + 3);
+                    c2 = (R)__ldg(cf + 4);
+                } else if (MODE == MODE_STEP) {
+                    c0 = (R)__ldg(cf + 2 + a.mom_step);
+                }
             }
         }
 
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
             const int ci = lane + q * G;
-            const bool on = FW || (active && ci < wc);
+            const bool on = active && ci < wc;
             const int64_t cofs = (int64_t)ci * K;
             if (on) uo[q] = load_chunk_ldg(u + orig * ldg + cofs);
             if (MODE == MODE_SECOND && on) xo[q] = load_chunk_cs(y + orig * ldy + cofs);
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
                     const int ci = lane + q * G;
-                    if (FW || (active && ci < wc))
+                    if (active && ci < wc)
                         g[e][q] = load_chunk_ldg(urow + (int64_t)ci * K);
                     else
                         zero_chunk(g[e][q]);
@@ -412,20 +414,18 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
             const Chunk hu = acc[q].value();  // (H u)_i
             Chunk wn;
             if (MODE == MODE_SPMV) {
-                wn = axpy_chunk(alpha_r, hu, scale_chunk(beta_r, uo[q]));
+                wn = axpy_chunk(alpha, hu, scale_chunk(beta, uo[q]));
                 store_chunk_cs(wp, wn);
             } else if (MODE == MODE_SECOND) {
                 // w = 2 alpha Hu + (2 beta u - x) ; y = c2 w + (c1 u + c0 x)
-                wn = axpy_chunk(two_alpha_r, hu,
-                                axpy_chunk(two_beta_r, uo[q], neg_chunk(xo[q])));
+                wn = axpy_chunk(two_alpha, hu, axpy_chunk(two_beta, uo[q], neg_chunk(xo[q])));
                 const Chunk yn =
-                    axpy_chunk(c2r, wn, axpy_chunk(c1r, uo[q], scale_chunk(c0r, xo[q])));
+                    axpy_chunk(c2, wn, axpy_chunk(c1, uo[q], scale_chunk(c0, xo[q])));
                 store_chunk_cs(wp, wn);
                 store_chunk_cs(yp, yn);
             } else {
-                wn = axpy_chunk(two_alpha_r, hu,
-                                axpy_chunk(two_beta_r, uo[q], neg_chunk(xo[q])));
-                const Chunk yn = axpy_chunk(c0r, wn, yo[q]);
+                wn = axpy_chunk(two_alpha, hu, axpy_chunk(two_beta, uo[q], neg_chunk(xo[q])));
+                const Chunk yn = axpy_chunk(c0, wn, yo[q]);
                 store_chunk_cs(wp, wn);
                 store_chunk_cs(yp, yn);
             }

@@ -161,10 +161,17 @@ chebfd_status chebfd_choose_params(const chebfd_matrix* H, double a, double b, d
         cudaFree(dx);
         cudaFree(dz);
         CHEBFD_REQUIRE(st == CHEBFD_OK, st, "MLP inference failed");
-        // outputs: log N_p, log n_s, kernel logit (> 0: Lanczos, else Jackson)
-        *Np = (int)std::max(8.0, std::min(20000.0, std::round(std::exp((double)z[0]))));
-        const int n_s = (int)std::ceil(std::exp((double)z[1]) / 4.0) * 4;
-        *ns = std::max(8, std::min(n_s, 1024));
+        // outputs are scale-free: log(N_p / N_p of the rule), log(n_s / N_T),
+        // kernel logit (> 0: Lanczos, else Jackson); each is kept inside the
+        // range the network was trained on (N_p ratio [1/2, 2], n_s/N_T [2, 6],
+        // the paper's 2 <= N_S/N_T recommendation at the low end)
+        int ns_rule = 0, np_rule = 0, k_rule = 0;
+        heuristic(H->m, A, lam_lo, lam_hi, &ns_rule, &np_rule, &k_rule);
+        const double rp = std::exp(std::max(std::log(0.5), std::min(std::log(2.0), (double)z[0])));
+        const double rs = std::exp(std::max(std::log(2.0), std::min(std::log(6.0), (double)z[1])));
+        *Np = (int)std::max(8.0, std::min(20000.0, std::round(rp * np_rule)));
+        const int n_s = (int)std::ceil(rs * std::max(A.n_target, 1.0) / 8.0) * 8;
+        *ns = std::max(16, std::min(n_s, 1024));
         *kernel = z[2] > 0.f ? CHEBFD_KERNEL_LANCZOS : CHEBFD_KERNEL_JACKSON;
     });
 }

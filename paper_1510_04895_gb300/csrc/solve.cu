@@ -111,6 +111,7 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
     std::vector<double> theta(ns), res(ns), prev_theta, prev_res;
     int64_t refill = 0;
     double prev_worst = -1.0;
+    bool prev_empty = false;
     double t_filter = 0.0, t_dense = 0.0;
     int it = 0, fp64_its = 0;
     bool converged = false;
@@ -149,6 +150,13 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
         double worst = 0.0;
         for (int k : acc_idx) worst = std::max(worst, res[k]);
         converged = !acc_idx.empty() && worst <= p.eps * normH;
+        // empty window: two successive iterations (ghosts recognised) accept nothing
+        const bool empty_now = !prev_theta.empty() && acc_idx.empty();
+        if (empty_now && prev_empty) {
+            converged = true;
+            break;
+        }
+        prev_empty = empty_now;
         if (converged && !single_phase) break;
         if (converged && single_phase) {
             // reached the target in single precision: confirm with one FP64 sweep

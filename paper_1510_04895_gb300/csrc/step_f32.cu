@@ -24,11 +24,11 @@ int blocks_per_sm(Kern kern, size_t smem) {
     return std::min(b, 8);
 }
 
-template <bool CPLX, int G, int CPT, int MODE, int L, bool FW>
+template <bool CPLX, int G, int CPT, int MODE, int L, bool ENS>
 void launch_l(const SellView& H, const StepArgs& a, int wc, int sms, cudaStream_t s) {
     constexpr int SLOTS = STEP_THREADS / G;
     const size_t smem = a.moments ? (size_t)SLOTS * 2 * a.nb * sizeof(double) : 0;
-    auto kern = cheb_step_kernel<float, CPLX, G, CPT, MODE, L, FW>;
+    auto kern = cheb_step_kernel<float, CPLX, G, CPT, MODE, L, ENS>;
     const int grid = sms * blocks_per_sm(kern, a.moments ? (size_t)16384 : 0);
     kern<<<grid, STEP_THREADS, smem, s>>>(H, a, wc);
 }
@@ -39,8 +39,12 @@ template <bool CPLX, int G, int CPT, int MODE>
 void launch_m(const SellView& H, const StepArgs& a, int wc, int width, int sms,
               cudaStream_t s) {
     constexpr int L13 = CPT == 1 ? 13 : 0, L4 = CPT == 1 ? 4 : 0;
-    // (the full-width variant without lane predicates spills at 3 blocks/SM
-    // and measured slower, so only the predicated kernels are dispatched)
+    if (a.coef != nullptr) {
+        if (CPT == 1 && width == 13) launch_l<CPLX, G, CPT, MODE, L13, true>(H, a, wc, sms, s);
+        else if (CPT == 1 && width == 4) launch_l<CPLX, G, CPT, MODE, L4, true>(H, a, wc, sms, s);
+        else launch_l<CPLX, G, CPT, MODE, 0, true>(H, a, wc, sms, s);
+        return;
+    }
     if (CPT == 1 && width == 13) launch_l<CPLX, G, CPT, MODE, L13, false>(H, a, wc, sms, s);
     else if (CPT == 1 && width == 4) launch_l<CPLX, G, CPT, MODE, L4, false>(H, a, wc, sms, s);
     else launch_l<CPLX, G, CPT, MODE, 0, false>(H, a, wc, sms, s);

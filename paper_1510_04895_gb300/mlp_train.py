@@ -143,7 +143,8 @@ def load_records(path):
 
 
 def dataset(records):
-    """Features and targets (log N_p, log n_s, 1 if Lanczos) of the best correct run."""
+    """Features and scale-free targets of the best correct run: log(N_p / N_p of
+    the paper's rule), log(n_s / N_T estimate), 1 if the kernel is Lanczos."""
     X, T = [], []
     for rec in records:
         good = [r for r in rec["runs"] if r["correct"]]
@@ -151,7 +152,9 @@ def dataset(records):
             continue
         best = min(good, key=lambda r: r["cost"])
         X.append(rec["features"])
-        T.append([np.log(best["Np"]), np.log(best["ns"]), 1.0 if best["kernel"] == "lanczos" else 0.0])
+        T.append([np.log(best["Np"] / rec["heuristic"]["Np"]),
+                  np.log(best["ns"] / max(rec["n_target_kpm"], 1.0)),
+                  1.0 if best["kernel"] == "lanczos" else 0.0])
     return np.array(X, np.float32), np.array(T, np.float32)
 
 

@@ -140,6 +140,8 @@ def test_batched_solve_matches_dense_per_member(precision):
         r = res[i]
         normH = max(abs(a[i]), abs(b[i]))
         assert r["converged"] and r["nev"] == len(exact), (i, r["nev"], len(exact))
+        if not len(exact):
+            continue                      # a window inside this member's gap
         assert np.abs(np.sort(r["lam"]) - exact).max() <= 1e-10 * normH
         assert r["res"].max() <= 1e-9 * normH
         V = r["V"].cpu().numpy()

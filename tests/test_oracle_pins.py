@@ -445,3 +445,12 @@ def test_mlp_adam_reduces_loss_on_a_fittable_target():
         _, G = mlp.loss_and_grad(P, X, T)
         mlp.adam_step(P, G, st, 1e-2)
     assert mlp.loss(P, X, T) < 0.2 * L_start
+
+
+def test_chebfd_empty_window_terminates():
+    """A window inside a spectral gap holds no eigenvalue: the iteration stops
+    with no pairs after two iterations without in-window Ritz values."""
+    lam = np.concatenate([np.linspace(-1, -0.2, 300), np.linspace(0.2, 1, 300)])
+    H = sp.diags(lam).tocsr()
+    r = solve.chebfd(H, -1.01, 1.01, -0.05, 0.05, 16, 60, 1e-9, complex_values=False)
+    assert r["converged"] and len(r["theta"]) == 0 and r["iterations"] <= 4
