@@ -167,6 +167,13 @@ def barrier(world):
         dist.barrier()
 
 
+def aggregate(world, units_per_rank, t_local):
+    """Whole-job throughput: every rank did units_per_rank units; the job took
+    the slowest rank's time.  Returns (units per second, max time)."""
+    t_max = barrier_max(world, t_local)
+    return world * units_per_rank / t_max, t_max
+
+
 # ------------------------------------------------------------------ CPU legs
 
 
@@ -367,9 +374,8 @@ def run_ours(args):
         torch.cuda.synchronize()
     t_dev = e0.elapsed_time(e1) / 1e3
     barrier(world)
-    t_max = barrier_max(world, t_dev)
     units_rank = N * ns * Np * args.steps
-    value = world * units_rank / t_max
+    value, t_max = aggregate(world, units_rank, t_dev)
     launches = args.steps * ((ns + nb - 1) // nb) * Np
 
     # ---- dominant kernel alone: the fused Chebyshev step (n_b = 64) ----------
