@@ -1,12 +1,18 @@
 #!/usr/bin/env python
 """Throughput of the ChebFD polynomial filter (Fig. ChebFD) on GB300.
 
-Workload: the 64x64x32x4 topological insulator (N = 524288, W = 1.0, seed 1),
-a search space of n_s = 256 vectors filtered in four row-major blocks of
-n_b = 64, complex64 recurrence with FP32 accumulation, Lanczos kernel (mu = 2),
-central window [-delta, delta] holding ~100 eigenpairs (oracle KPM, frozen in
-tests/golden/topi_64x64x32_window.txt), N_p from the Lanczos-kernel scaling
-N_p = N_0 S_w / delta' with N_0 = 6.23 and delta' = delta (N_S = 4 N_T, linear DOS).
+Default workload (--workload topi): the 64x64x32x4 topological insulator
+(N = 524288, W = 1.0, seed 1), a search space of n_s = 256 vectors filtered in
+four row-major blocks of n_b = 64, complex64 recurrence with FP32
+accumulation, Lanczos kernel (mu = 2), central window [-delta, delta] holding
+~100 eigenpairs (oracle KPM, frozen in tests/golden/topi_64x64x32_window.txt),
+N_p from the Lanczos-kernel scaling N_p = N_0 S_w / delta' with N_0 = 6.23 and
+delta' = (sqrt(N_S / N_T) - 1) delta (linear DOS, Sec. 2.4).
+
+--workload graphene: the 1024x1024 disordered honeycomb lattice (N = 2097152,
+real symmetric, W = 1.0, seed 2), n_s = 512 in four blocks of n_b = 128, FP32
+recurrence, window of ~200 eigenpairs (tests/golden/graphene_1024x1024_window.txt),
+N_p by the same rule with N_T = 200.
 
 One step = one application p[H] X of the degree-N_p filter to the whole
 search block.  metric = filter row-vector updates per second
@@ -25,16 +31,26 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WINDOW_FILE = os.path.join(ROOT, "tests", "golden", "topi_64x64x32_window.txt")
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "cheb_step_c64_nb64_topi64x64x32.txt")
 METRIC = "filter row-vector updates/s (N * n_s * N_p / t)"
 UNIT = "row-vector updates/s"
 N0_LANCZOS = 6.23
 
+# Per workload: lattice (from workloads), frozen window, KPM target count N_T,
+# stored entries per row, value type, and the ncu summary of its fused step.
+WORKLOADS = {
+    "topi": dict(spec="TOPI_MEDIUM", window="topi_64x64x32_window.txt", NT=100, nnz_row=13,
+                 cplx=True, label="topi 64x64x32x4 (N=524288) W=1.0 seed 1",
+                 profile="cheb_step_c64_nb64_topi64x64x32.txt", profile_nb=64,
+                 profile_blocked="bell_step_c64_nb64_topi64x64x32.txt"),
+    "graphene": dict(spec="GRAPHENE", window="graphene_1024x1024_window.txt", NT=200, nnz_row=4,
+                     cplx=False, label="graphene 1024x1024x2 (N=2097152) W=1.0 seed 2",
+                     profile="cheb_step_r32_nb128_graphene1024x1024.txt", profile_nb=128),
+}
 
-def load_window():
+
+def load_window(name="topi"):
     vals = {}
-    with open(WINDOW_FILE) as f:
+    with open(os.path.join(ROOT, "tests", "golden", WORKLOADS[name]["window"])) as f:
         for line in f:
             if line.strip() and not line.startswith("#"):
                 k, v = line.split()
@@ -44,30 +60,33 @@ def load_window():
 
 def workload_params(args):
     """N_p by the rule of Sec. 3.1 step 3 / Sec. 2.4: the search-interval margin
-    delta' follows from N_S = 256 and the KPM count N_T ~ 100 for the linear DOS
-    of the insulator (delta'/delta = sqrt(N_S/N_T) - 1), and
+    delta' follows from N_S and the KPM count N_T for the linear DOS of the
+    insulator and of graphene (delta'/delta = sqrt(N_S/N_T) - 1), and
     N_p = N_0 S_w / delta' with N_0 = 6.23 (Tab. lanczoskernel, centre)."""
     from paper_1510_04895_gb300 import workloads
-    w = dict(workloads.TOPI_MEDIUM)
-    a, b, delta = load_window()
+    name = getattr(args, "workload", "topi")
+    spec = WORKLOADS[name]
+    w = dict(getattr(workloads, spec["spec"]), **spec)
+    a, b, delta = load_window(name)
     S_w = 0.5 * (b - a)
-    margin = (np.sqrt(w["ns"] / 100.0) - 1.0) * delta
+    margin = (np.sqrt(w["ns"] / float(spec["NT"])) - 1.0) * delta
     Np = args.Np or int(round(N0_LANCZOS * S_w / margin))
     return w, a, b, delta, Np
 
 
-def read_traffic():
+def read_traffic(profile):
     """DRAM bytes per launch of the fused step from the committed ncu summary,
     or None when the kernel source changed since that capture."""
     import hashlib
     vals = {}
     try:
-        with open(PROFILE_TRAFFIC) as f:
+        with open(os.path.join(ROOT, "profiles", profile)) as f:
             for line in f:
                 if line.strip() and not line.startswith("#"):
                     parts = line.split()
                     vals[parts[0]] = parts[1] if len(parts) > 1 else ""
-        src = os.path.join(ROOT, "paper_1510_04895_gb300", "csrc", "filter_kernels.cuh")
+        src = os.path.join(ROOT, vals.get("kernel_source",
+                                          "paper_1510_04895_gb300/csrc/filter_kernels.cuh"))
         with open(src, "rb") as f:
             digest = hashlib.sha256(f.read()).hexdigest()[:16]
     except OSError:
@@ -182,17 +201,22 @@ def oracle_sample(w, a, b, delta, steps_per_sample, nb=64, seed=0):
     same matrix: returns (row-vector updates/s, seconds, description)."""
     from oracle import coeffs, filter as ofilt, lattice
     from paper_1510_04895_gb300 import workloads
-    Ho = lattice.to_scipy(*lattice.topi_csr(w["Lx"], w["Ly"], w["Lz"], t=w["t"], m=w["m"],
-                                            W=w["W"], seed=w["seed"]))
+    if w["kind"] == "topi":
+        csr = lattice.topi_csr(w["Lx"], w["Ly"], w["Lz"], t=w["t"], m=w["m"], W=w["W"],
+                               seed=w["seed"])
+    else:
+        csr = lattice.graphene_csr(w["Lx"], w["Ly"], t=w["t"], W=w["W"], seed=w["seed"])
+    Ho = lattice.to_scipy(*csr)
     alpha, beta = coeffs.scaling(a, b)
     gc = coeffs.filter_coeffs(a, b, -delta, delta, steps_per_sample, "lanczos")
-    X = workloads.random_block(seed, Ho.shape[0], nb, True)
+    X = workloads.random_block(seed, Ho.shape[0], nb, w["cplx"])
     t0 = time.perf_counter()
     ofilt.filter_block(Ho, alpha, beta, gc, X)
     dt = time.perf_counter() - t0
     units = Ho.shape[0] * nb * steps_per_sample
-    desc = ("oracle FP64 complex128 filter, %d Chebyshev steps on one %d-vector block of the "
-            "N=%d matrix (scipy CSR product, single thread)" % (steps_per_sample, nb, Ho.shape[0]))
+    desc = ("oracle FP64 %s filter, %d Chebyshev steps on one %d-vector block of the "
+            "N=%d matrix (scipy CSR product, single thread)" % (
+                "complex128" if w["cplx"] else "float64", steps_per_sample, nb, Ho.shape[0]))
     return units / dt, dt, desc
 
 
@@ -210,9 +234,9 @@ def run_reference(args):
     ms = 1e3 * statistics.median(dt for _, dt in samples)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": "topi 64x64x32x4 (N=524288) W=1.0 seed 1, n_b=64, window "
-                                   "[-%.6g, %.6g]" % (delta, delta)},
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128" if w["cplx"] else "f64",
+            "data": "synthetic",
+            "config": {"workload": "%s, n_b=64, window [-%.6g, %.6g]" % (w["label"], delta, delta)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -270,11 +294,11 @@ def bench_ensemble(pkg, workloads, dev, peak_gbs):
             "autotune_ms_per_step": ms_step_tune}
 
 
-def bench_solve(pkg, H, a, b, delta, Np, ns, eps=1e-9):
+def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chiral=True):
     """Wall time of the whole ChebFD solve (Sec. 3.1 steps 4-8) to residual
     <= eps ||H|| for every accepted pair in [-delta, delta]: plain FP64 against
-    the mixed form (complex64 filter until the residuals stall, then FP64
-    sweeps; FP64 Gram, Rayleigh-Ritz and residuals throughout)."""
+    the mixed form (single-precision filter until the residuals stall, then
+    FP64 sweeps; FP64 Gram, Rayleigh-Ritz and residuals throughout)."""
     import torch
     out = {}
     lams = {}
@@ -293,12 +317,14 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, eps=1e-9):
                      "converged": r["converged"], "max_residual_over_normH":
                          float(r["res"].max() / normH) if r["nev"] else None,
                      "seconds_filter": r["seconds_filter"], "seconds_dense": r["seconds_dense"],
-                     "n_mvm": r["n_mvm"],
-                     "chiral_pairing_error": float(np.abs(lam + lam[::-1]).max()) if r["nev"] else None}
+                     "n_mvm": r["n_mvm"]}
+        if chiral and r["nev"]:
+            # spec(H) = -spec(H) for the insulator: the window set is +- paired
+            out[prec]["chiral_pairing_error"] = float(np.abs(lam + lam[::-1]).max())
     # learned parameters: (N_p, n_s, kernel) from the trained MLP on the KPM
     # features of this matrix and window, with the mixed-precision solve
     wpath = os.path.join(ROOT, "paper_1510_04895_gb300", "data", "mlp_weights.npy")
-    if os.path.exists(wpath):
+    if learned and os.path.exists(wpath):
         from paper_1510_04895_gb300 import mlp_train
         net = pkg.MLP(mlp_train.N_IN, 128)
         net.set_params(np.load(wpath).astype(np.float32))
@@ -329,8 +355,8 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, eps=1e-9):
     if len(lams["fp64"]) == len(lams["mixed"]) and len(lams["fp64"]):
         out["max_eigenvalue_difference"] = float(np.abs(lams["fp64"] - lams["mixed"]).max())
     out["eps"] = eps
-    out["workload"] = "topi 64x64x32x4, window [-%.6g, %.6g], n_s = %d, N_p = %d, Lanczos mu=2" % (
-        delta, delta, ns, Np)
+    out["workload"] = "%s, window [-%.6g, %.6g], n_s = %d, N_p = %d, Lanczos mu=2" % (
+        label, delta, delta, ns, Np)
     return out
 
 
@@ -344,20 +370,27 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w, a, b, delta, Np = workload_params(args)
-    ns, nb = w["ns"], args.nb
-    H = pkg.chebfd_matrix_create_lattice("topi", w["Lx"], w["Ly"], w["Lz"], t=w["t"], m=w["m"],
-                                         W=w["W"], seed=w["seed"], sell_C=args.sell_C,
+    cplx = w["cplx"]
+    ns = w["ns"]
+    single = args.precision in ("single", "c64", "r32")
+    dtype_name = ("c64" if single else "c128") if cplx else ("r32" if single else "r64")
+    panel = min(ns, {"c64": 64, "c128": 32, "r32": 128, "r64": 128}[dtype_name])
+    nb = args.nb or panel
+    H = pkg.chebfd_matrix_create_lattice(w["kind"], w["Lx"], w["Ly"], w["Lz"], t=w["t"],
+                                         m=w["m"], W=w["W"], seed=w["seed"], sell_C=args.sell_C,
                                          also_single=True)
     N = H.n
     alpha, beta = 2.0 / (b - a), (a + b) / (a - b)
     gc = pkg.chebfd_window_coeffs(a, b, -delta, delta, Np, "lanczos", 2.0)
-    cdt = torch.complex64 if args.precision == "c64" else torch.complex128
+    cdt = {"c64": torch.complex64, "c128": torch.complex128, "r32": torch.float32,
+           "r64": torch.float64}[dtype_name]
     X = torch.empty((N, ns), dtype=cdt, device=dev)
     pkg.chebfd_random_block(X, col0=0, ns_total=ns, seed=rank)
-    # the library splits the 256 columns into row-major panels of n_b
     stream = torch.cuda.current_stream()
 
     def step():
+        # the library filters the n_s columns in row-major panels of its
+        # widest panel for the value type (complex64 64, complex128 32, real 128)
         pkg.chebfd_filter_block(H, alpha, beta, gc, X)
 
     for _ in range(args.warmup):
@@ -376,41 +409,56 @@ def run_ours(args):
     barrier(world)
     units_rank = N * ns * Np * args.steps
     value, t_max = aggregate(world, units_rank, t_dev)
-    launches = args.steps * ((ns + nb - 1) // nb) * Np
+    launches = args.steps * ((ns + panel - 1) // panel) * Np
 
-    # ---- dominant kernel alone: the fused Chebyshev step (n_b = 64) ----------
+    # ---- dominant kernel alone: the fused Chebyshev step on one n_b block ------
     U = torch.empty((N, nb), dtype=cdt, device=dev)
     Wv = torch.empty_like(U)
     Y = torch.empty_like(U)
     pkg.chebfd_random_block(U, ns_total=nb, seed=11)
     pkg.chebfd_random_block(Wv, ns_total=nb, seed=12)
     Y.zero_()
-    for _ in range(5):
-        pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, U, Wv, Y)
-    reps = 50
-    torch.cuda.synchronize()
-    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    k0.record(stream)
-    for i in range(reps):
-        if i % 2 == 0:
+
+    def time_step(reps=50):
+        for _ in range(5):
             pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, U, Wv, Y)
-        else:
-            pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, Wv, U, Y)
-    k1.record(stream)
-    torch.cuda.synchronize()
-    t_launch = k0.elapsed_time(k1) / 1e3 / reps
-    S_v = 8 if cdt == torch.complex64 else 16
-    S_d = S_v
-    nnz_row = 13
-    bytes_launch = N * (nnz_row * (S_d + 4) + 5 * nb * S_v)
+        torch.cuda.synchronize()
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for i in range(reps):
+            if i % 2 == 0:
+                pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, U, Wv, Y)
+            else:
+                pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, Wv, U, Y)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        return k0.elapsed_time(k1) / 1e3 / reps
+
+    blocked = single and H.blocked_width > 0
+    t_launch = time_step()
+    S_v = U.element_size()                      # bytes of one vector entry
+    S_d = S_v                                   # matrix values stored at the same precision
+    bytes_launch = N * (w["nnz_row"] * (S_d + 4) + 5 * nb * S_v)
     peaks, peak_kind = measured_peaks()
     achieved = bytes_launch / t_launch / 1e9
-    traffic = read_traffic() if cdt == torch.complex64 and nb == 64 else None
+    kname = "bell_step_kernel" if blocked else "cheb_step_kernel"
+    profile = w.get("profile_blocked") if blocked else w["profile"]
+    traffic = read_traffic(profile) if profile and single and nb == w["profile_nb"] else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "kernel": "cheb_step_kernel (MODE_STEP, %s, n_b=%d)" % (args.precision, nb),
+            "kernel": "%s (MODE_STEP, %s, n_b=%d)" % (kname, dtype_name, nb),
             "bytes_per_launch": bytes_launch, "launch_us": t_launch * 1e6,
             "peak_kind": peak_kind + " (burst copy)"}
+    if blocked:
+        # the same step on the SELL arrays alone (row-wise kernel)
+        H.set_blocked(False)
+        t_sell = time_step()
+        H.set_blocked(True)
+        roof["sell_kernel"] = {"kernel": "cheb_step_kernel (MODE_STEP, %s, n_b=%d)" % (
+            dtype_name, nb), "launch_us": t_sell * 1e6,
+            "achieved": bytes_launch / t_sell / 1e9,
+            "frac": bytes_launch / t_sell / 1e9 / peaks["hbm_gbs"]}
+    del U, Wv, Y
 
     # ---- end to end through the C ABI with host buffers ------------------------
     Xh = torch.empty((N, ns), dtype=cdt, pin_memory=True)
@@ -429,12 +477,13 @@ def run_ours(args):
     e2e = {"value": world * N * ns * Np / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": X.numel() * X.element_size(),
            "d2h_bytes_per_step": X.numel() * X.element_size()}
+    del Xd, Xh
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": args.precision, "data": "synthetic",
-           "config": {"workload": "topi 64x64x32x4 (N=524288) W=1.0 seed 1", "n_s": ns, "n_b": nb,
+           "dtype": dtype_name, "data": "synthetic",
+           "config": {"workload": w["label"], "n_s": ns, "n_b": panel,
                       "N_p": Np, "kernel": "lanczos mu=2",
                       "window": [-delta, delta], "spectral_interval": [a, b],
                       "sell_C": args.sell_C,
@@ -444,11 +493,15 @@ def run_ours(args):
            "roofline": roof, "e2e": e2e, "gpu_launches": launches,
            "clocks": clk.summary(),
            "hbm_gbs_filter_region": bytes_launch * launches / t_max / 1e9}
+    del X
 
-    if not args.no_ensemble:
+    if not args.no_ensemble and w["kind"] == "topi":
         out["ensemble"] = bench_ensemble(pkg, workloads, dev, peaks["hbm_gbs"])
     if not args.no_solve:
-        out["time_to_solution"] = bench_solve(pkg, H, a, b, delta, Np, w["ns"])
+        # the MLP was trained on insulators only: learned parameters for those
+        out["time_to_solution"] = bench_solve(pkg, H, a, b, delta, Np, ns, w["label"],
+                                              learned=w["kind"] == "topi",
+                                              chiral=w["kind"] == "topi")
 
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, desc = oracle_sample(w, a, b, delta, args.cpu_steps)
@@ -468,8 +521,10 @@ def main():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--nb", type=int, default=64)
-    p.add_argument("--precision", default="c64", choices=["c64", "c128"])
+    p.add_argument("--workload", default="topi", choices=sorted(WORKLOADS))
+    p.add_argument("--nb", type=int, default=0, help="block width (0: the workload's)")
+    p.add_argument("--precision", default="single",
+                   choices=["single", "double", "c64", "c128", "r32", "r64"])
     p.add_argument("--Np", type=int, default=0)
     p.add_argument("--sell-C", dest="sell_C", type=int, default=1)
     p.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=8)

@@ -106,7 +106,7 @@ typedef struct chebfd_matrix_info {
     int32_t max_row_len;
     int32_t is_complex;   /* values C128 (and C64) if nonzero, else R64 (and R32) */
     int32_t has_single;   /* a single-precision copy of the values exists */
-    int32_t reserved;
+    int32_t blocked_width; /* block columns per 4-row block of the blocked copy, 0 if none */
 } chebfd_matrix_info;
 
 /* ------------------------------------------------------------------ basics */
@@ -145,6 +145,24 @@ chebfd_status chebfd_matrix_get_info(const chebfd_matrix* H, chebfd_matrix_info*
 chebfd_status chebfd_matrix_export_sell(const chebfd_matrix* H, int64_t* chunk_ptr,
                                         int32_t* chunk_len, int32_t* col, void* val,
                                         int64_t* perm);
+
+/* Blocked copy.  A complex matrix built with also_single, sell_sigma = 1 and
+ * n divisible by 4 whose blocks of 4 consecutive rows (the orbitals of one
+ * lattice site, Sec. 4's topological insulator) each couple to at most 7
+ * blocks of 4 columns and hold on average at least 28 stored entries (so the
+ * dense blocks store at most 4x the entries) also gets a blocked-ELL copy:
+ * per row block, 7 block columns (own block first) with dense 4x4 complex64
+ * blocks (zeros stored).
+ * The complex64 Chebyshev step (chebfd_chebyshev_step and the loop of
+ * chebfd_filter_block) then reads that copy and computes the 4 rows of a
+ * block together, gathering each neighbour row of u once per block instead
+ * of once per row; results agree with the SELL kernel to FP32 rounding.  It
+ * costs 7 * 16 * 8 = 896 bytes per 4 rows of device memory.  The copy is not
+ * built when the environment variable CHEBFD_BLOCKED is "0" at creation.
+ * chebfd_matrix_set_blocked(H, 0) makes the kernels use the SELL arrays only;
+ * (H, 1) uses the copy again (EUNSUPPORTED if there is none).  Not thread-safe
+ * against kernels of H in flight on other host threads. */
+chebfd_status chebfd_matrix_set_blocked(chebfd_matrix* H, int enable);
 
 chebfd_status chebfd_matrix_destroy(chebfd_matrix* H);
 
@@ -197,6 +215,23 @@ chebfd_status chebfd_window_coeffs(double a, double b, double lam_lo, double lam
 chebfd_status chebfd_filter_block(const chebfd_matrix* H, double alpha, double beta,
                                   const double* gc, int Np, void* X, int64_t ld, int nb,
                                   chebfd_dtype vdt, double* moments, void* stream);
+
+/* chebfd_filter_block computed in double-float arithmetic for an FP64 block
+ * (vdt C128 or R64 matching H): every entry and matrix value is carried as an
+ * unevaluated sum hi + lo of two floats (48-bit significand, unit roundoff
+ * ~2^-48 against FP64's 2^-53) and all products and sums use error-free
+ * FP32 transformations (TwoSum, FMA TwoProduct) on the paired FP32 pipe,
+ * which GB300 executes ~64x faster than FP64.  The block is split into
+ * hi/lo panels of 32 complex or 64 real columns, filtered (Fig. ChebFD, the
+ * same three step kinds as chebfd_filter_block) and summed back into FP64.
+ * Entries must stay inside the FP32 exponent range (|x| < 3e38; the
+ * recurrence keeps |T_n(A) x| <= ||x|| while spec(H) lies in [a, b]).
+ * Needs a matrix built with also_single (the double-float value copy is built
+ * with the FP32 copy).  No moments.  Work panels come from the stream-ordered
+ * allocator.  Asynchronous on `stream`.  EINVAL on bad arguments. */
+chebfd_status chebfd_filter_block_df(const chebfd_matrix* H, double alpha, double beta,
+                                     const double* gc, int Np, void* X, int64_t ld, int nb,
+                                     chebfd_dtype vdt, void* stream);
 
 /* Same contract and results as chebfd_filter_block, for callers that cannot
  * allocate device memory at this point: for instance code that runs while
@@ -403,8 +438,10 @@ chebfd_status chebfd_mlp_destroy(chebfd_mlp* N);
 
 typedef enum chebfd_precision {
     CHEBFD_PRECISION_FP64 = 0,  /* FP64 filter, FP64 orthonormalisation and Rayleigh-Ritz */
-    CHEBFD_PRECISION_MIXED = 1  /* FP32 / complex64 filter until the residuals stall, then
+    CHEBFD_PRECISION_MIXED = 1, /* FP32 / complex64 filter until the residuals stall, then
                                    FP64 filter sweeps; FP64 orthonormalisation, RR, residuals */
+    CHEBFD_PRECISION_MIXED_DF = 2 /* as MIXED, but the sweeps after the stall run the
+                                   double-float filter (chebfd_filter_block_df) */
 } chebfd_precision;
 
 /* Parameters of chebfd_solve.  Zero / negative fields take the defaults given. */
@@ -452,7 +489,7 @@ typedef struct chebfd_result_info {
     int32_t nev;
     int32_t iterations;
     int32_t converged;
-    int32_t fp64_iterations;    /* iterations whose filter ran in FP64 */
+    int32_t fp64_iterations;    /* iterations whose filter ran in FP64 (double-float in MIXED_DF) */
     int64_t n_mvm;              /* N_iter * N_S * N_p products with H (vector count) */
     double a, b;                /* spectral interval used */
     double seconds_filter, seconds_dense, seconds_total;

@@ -21,6 +21,8 @@ KERNEL_IDS = {"none": KERNEL_NONE, "fejer": KERNEL_FEJER, "jackson": KERNEL_JACK
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "ENOCONV",
           6: "ETIMEOUT", 7: "EUNSUPPORTED"}
 
+PRECISION = {"fp64": 0, "mixed": 1, "mixed_df": 2}
+
 c_i64p = ctypes.POINTER(ctypes.c_int64)
 c_i32p = ctypes.POINTER(ctypes.c_int32)
 c_dp = ctypes.POINTER(ctypes.c_double)
@@ -39,7 +41,7 @@ class MatrixInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_padded", ctypes.c_int64),
                 ("nchunks", ctypes.c_int64), ("C", ctypes.c_int32), ("sigma", ctypes.c_int32),
                 ("max_row_len", ctypes.c_int32), ("is_complex", ctypes.c_int32),
-                ("has_single", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("has_single", ctypes.c_int32), ("blocked_width", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); every function returns chebfd_status unless noted
@@ -55,6 +57,7 @@ SIGNATURES = {
     "chebfd_matrix_get_info": (ctypes.c_int, [c_vp, ctypes.POINTER(MatrixInfo)]),
     "chebfd_matrix_export_sell": (ctypes.c_int, [c_vp, c_i64p, c_i32p, c_i32p, c_vp, c_i64p]),
     "chebfd_matrix_destroy": (ctypes.c_int, [c_vp]),
+    "chebfd_matrix_set_blocked": (ctypes.c_int, [c_vp, ctypes.c_int]),
     "chebfd_spmv": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double, c_vp, c_vp,
                                    ctypes.c_int64, ctypes.c_int, ctypes.c_int, c_vp]),
     "chebfd_scale_bounds": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_uint64, c_dp, c_dp, c_dp,
@@ -68,6 +71,9 @@ SIGNATURES = {
     "chebfd_filter_block_noalloc": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double, c_dp,
                                                    ctypes.c_int, c_vp, ctypes.c_int64,
                                                    ctypes.c_int, ctypes.c_int, c_dp, c_vp]),
+    "chebfd_filter_block_df": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double, c_dp,
+                                              ctypes.c_int, c_vp, ctypes.c_int64, ctypes.c_int,
+                                              ctypes.c_int, c_vp]),
     "chebfd_chebyshev_step": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, c_vp, c_vp, c_vp, ctypes.c_int64,
                                              ctypes.c_int, ctypes.c_int, c_vp]),
@@ -214,6 +220,16 @@ class Matrix:
     def is_complex(self):
         return bool(self.info.is_complex)
 
+    @property
+    def blocked_width(self):
+        """Block columns per 4-row block of the blocked copy (0: no copy)."""
+        return self.info.blocked_width
+
+    def set_blocked(self, enable):
+        """Use (True) or bypass (False) the blocked copy in the complex64 step."""
+        _check(lib().chebfd_matrix_set_blocked(self.handle, 1 if enable else 0),
+               "chebfd_matrix_set_blocked")
+
     def close(self):
         if self.handle:
             _check(lib().chebfd_matrix_destroy(self.handle), "chebfd_matrix_destroy")
@@ -312,6 +328,16 @@ def chebfd_filter_block_noalloc(H, alpha, beta, gc, X, moments=None, stream=None
                                              _stream(stream)), "chebfd_filter_block_noalloc")
 
 
+def chebfd_filter_block_df(H, alpha, beta, gc, X, stream=None):
+    """In place, double-float arithmetic: X <- p[H] X for an FP64 device block X."""
+    gc = np.ascontiguousarray(gc, np.float64)
+    Np = len(gc) - 1
+    n, nb = X.shape[0], X.shape[1]
+    _check(lib().chebfd_filter_block_df(H.handle, alpha, beta, gc.ctypes.data_as(c_dp), Np,
+                                        _ptr(X), X.stride(0), nb, dtype_of(X), _stream(stream)),
+           "chebfd_filter_block_df")
+
+
 def chebfd_chebyshev_step(H, alpha, beta, c, U, W, Y, stream=None):
     """W <- 2(alpha H + beta) U - W ; Y <- Y + c W (one fused step)."""
     n, nb = U.shape[0], U.shape[1]
@@ -374,7 +400,7 @@ def chebfd_solve(H, lam_lo, lam_hi, ns, Np, eps=1e-9, kernel="lanczos", mu=2.0, 
     import torch
     p = Params(lam_lo=lam_lo, lam_hi=lam_hi, eps=eps, a=a, b=b, mu=mu, ns=ns, Np=Np,
                kernel=KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel), nb=nb,
-               precision=1 if precision == "mixed" else 0, max_iter=max_iter,
+               precision=PRECISION[precision], max_iter=max_iter,
                lanczos_steps=lanczos_steps, reserved=0, seed=seed)
     h = c_vp()
     st = lib().chebfd_solve(H.handle, ctypes.byref(p), _stream(stream), ctypes.byref(h))
@@ -502,7 +528,7 @@ def chebfd_solve_batched(E, matrices, a, b, lam_lo, lam_hi, ns, Np, eps=1e-9, ke
     b = np.ascontiguousarray(b, np.float64)
     p = Params(lam_lo=lam_lo, lam_hi=lam_hi, eps=eps, a=0.0, b=0.0, mu=mu, ns=ns, Np=Np,
                kernel=KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel), nb=0,
-               precision=1 if precision == "mixed" else 0, max_iter=max_iter, lanczos_steps=0,
+               precision=PRECISION[precision], max_iter=max_iter, lanczos_steps=0,
                reserved=0, seed=seed)
     outs = (c_vp * cnt)()
     its = ctypes.c_int32()

@@ -19,6 +19,8 @@ void spmv_impl(const Matrix& M, double alpha, double beta, const void* X, void* 
                int nb, chebfd_dtype dt, cudaStream_t s);
 void kpm_impl(const Matrix& M, double alpha, double beta, int Mm, int R, uint64_t seed,
               double* mu, cudaStream_t s);
+void filter_block_df_impl(const Matrix& M, double alpha, double beta, const double* gc, int Np,
+                          void* X, int64_t ld, int nb, cudaStream_t s);
 void chebyshev_step_impl(const Matrix& M, double alpha, double beta, double c, const void* U,
                          void* W, void* Y, int64_t ld, int nb, chebfd_dtype dt, cudaStream_t s);
 
@@ -32,6 +34,9 @@ void free_matrix(Matrix& m) {
     cudaFree(m.perm);
     cudaFree(m.val64);
     cudaFree(m.val32);
+    cudaFree(m.valdf);
+    cudaFree(m.bell_col);
+    cudaFree(m.bell_val32);
     m = Matrix{};
 }
 
@@ -490,6 +495,16 @@ chebfd_status chebfd_matrix_get_info(const chebfd_matrix* H, chebfd_matrix_info*
         out->max_row_len = M.max_row_len;
         out->is_complex = M.complex_values ? 1 : 0;
         out->has_single = M.val32 ? 1 : 0;
+        out->blocked_width = M.bell_col ? kBellLB : 0;
+    });
+}
+
+chebfd_status chebfd_matrix_set_blocked(chebfd_matrix* H, int enable) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(H, CHEBFD_EINVAL, "null matrix");
+        CHEBFD_REQUIRE(!enable || H->m.bell_col, CHEBFD_EUNSUPPORTED,
+                       "matrix has no blocked copy");
+        H->m.bell_enabled = enable != 0;
     });
 }
 
@@ -596,6 +611,17 @@ chebfd_status chebfd_filter_block(const chebfd_matrix* H, double alpha, double b
         CHEBFD_REQUIRE(H, CHEBFD_EINVAL, "null matrix");
         filter_block_impl(H->m, alpha, beta, gc, Np, X, ld, nb, vdt, moments,
                           as_stream(stream));
+    });
+}
+
+chebfd_status chebfd_filter_block_df(const chebfd_matrix* H, double alpha, double beta,
+                                     const double* gc, int Np, void* X, int64_t ld, int nb,
+                                     chebfd_dtype vdt, void* stream) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(H, CHEBFD_EINVAL, "null matrix");
+        CHEBFD_REQUIRE(vdt == (H->m.complex_values ? CHEBFD_C128 : CHEBFD_R64), CHEBFD_EINVAL,
+                       "double-float filter takes the matrix's FP64 vector type");
+        filter_block_df_impl(H->m, alpha, beta, gc, Np, X, ld, nb, as_stream(stream));
     });
 }
 

@@ -85,16 +85,40 @@ struct Matrix {
     int64_t* perm = nullptr;       // [n], original row of sorted row r
     void* val64 = nullptr;         // double or double2 [nnz_padded]
     void* val32 = nullptr;         // float or float2 [nnz_padded], optional
+    // Double-float copy of the values [nnz_padded], built with val32: complex
+    // float4 (re_hi, re_lo, im_hi, im_lo), real float2 (hi, lo).
+    void* valdf = nullptr;
+    // Blocked-ELL copy of a complex matrix whose rows fall into blocks of
+    // kBellB consecutive rows that couple to at most kBellLB blocks of
+    // columns each (the 4 orbitals of a lattice site and its 6 neighbours):
+    // bell_col[nbr][kBellLB] block columns (slot 0 is the own block row,
+    // unused slots repeat it with zero values), bell_val32[nbr][kBellLB][b][b]
+    // dense complex64 blocks, row-major.  Built only with also_single and
+    // identity row order; used by the single-precision step kernel.
+    int32_t* bell_col = nullptr;
+    void* bell_val32 = nullptr;
+    bool bell_enabled = false;
     // Row panel order used by the kernels (same as sorted order here).
     int device = 0;
     int num_sms = 0;
 };
+
+constexpr int kBellB = 4;   // rows per block (orbitals per site)
+constexpr int kBellLB = 7;  // block columns per block row (own site + 6 neighbours)
 
 // Build the SELL arrays from a device CSR (rowptr[n+1], col, FP64 values).
 // Takes ownership of nothing; the CSR buffers may be freed afterwards.
 void build_sell_from_device_csr(Matrix& M, const int64_t* d_rowptr, const int32_t* d_col,
                                 const void* d_val, int C, int sigma, bool also_single,
                                 cudaStream_t stream);
+
+// Resident blocks per SM of a kernel at `threads` threads and `smem` dynamic
+// shared bytes on the current device (occupancy API, cached per kernel); >= 1.
+int cached_occupancy(const void* kernel, int threads, size_t smem);
+
+// Blocked-ELL copy (bell_col, bell_val32) when the CSR has that shape; no-op otherwise.
+void build_bell(Matrix& M, const int64_t* d_rowptr, const int32_t* d_col, const double* d_val,
+                cudaStream_t stream);
 
 void generate_lattice_csr(const chebfd_lattice_desc& d, int64_t* n_out, int64_t** d_rowptr,
                           int32_t** d_col, void** d_val, cudaStream_t stream);

@@ -2,6 +2,9 @@
 // plain product Y = (alpha H + beta) X, KPM moments and random blocks.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "filter_kernels.cuh"
@@ -12,6 +15,9 @@ void launch_step_f64(const SellView& H, bool cplx, StepMode mode, const StepArgs
                      int width, int sms, cudaStream_t s);
 void launch_step_f32(const SellView& H, bool cplx, StepMode mode, const StepArgs& a, int wc,
                      int width, int sms, cudaStream_t s);
+bool bell_step_applies(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs& a,
+                       int wc);
+void launch_bell_step(const Matrix& M, const StepArgs& a, int wc, cudaStream_t s);
 
 namespace {
 
@@ -24,6 +30,9 @@ SellView view_of(const Matrix& M, bool single) {
     v.perm = M.identity_perm ? nullptr : M.perm;
     v.n = M.n;
     v.C = M.C;
+    v.logC = 0;
+    while ((1 << v.logC) < M.C) ++v.logC;
+    CHEBFD_REQUIRE((1 << v.logC) == M.C, CHEBFD_EINVAL, "SELL chunk height must be a power of two");
     return v;
 }
 
@@ -31,6 +40,24 @@ SellView view_of(const Matrix& M, bool single) {
 int chunks_per_row(chebfd_dtype dt, int nb) { return (int)((size_t)nb * dtype_size(dt) / 16); }
 
 }  // namespace
+
+int cached_occupancy(const void* kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+    int dev = 0;
+    CHEBFD_CHECK_CUDA(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, kernel, threads, smem);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) !=
+            cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    cache[key] = occ;
+    return occ;
+}
 
 int max_panel_width(chebfd_dtype dt) {
     // 64 chunks of 16 bytes per row group: 64 complex doubles, 128 complex floats,
@@ -62,6 +89,11 @@ void launch_step(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs
                  cudaStream_t stream) {
     const int wc = chunks_per_row(dt, a.nb);
     CHEBFD_REQUIRE(wc >= 1 && wc <= 64, CHEBFD_EINVAL, "panel too wide for one row group");
+    if (bell_step_applies(M, dt, mode, a, wc)) {
+        launch_bell_step(M, a, wc, stream);
+        CHEBFD_CHECK_CUDA(cudaGetLastError());
+        return;
+    }
     const SellView v = view_of(M, is_single(dt));
     StepArgs args = a;
     if (args.tile <= 0) {

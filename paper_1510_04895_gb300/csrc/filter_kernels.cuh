@@ -197,6 +197,7 @@ struct SellView {
     const int64_t* perm;  // nullptr when identity
     int64_t n;
     int C;
+    int logC;  // C is a power of two: chunk of row r = r >> logC
 };
 
 constexpr int STEP_THREADS = 256;
@@ -256,18 +257,21 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
     const int64_t wave_rows = (int64_t)gridDim.x * tile * SLOTS;
     const int iters = (int)((H.n + wave_rows - 1) / wave_rows) * tile;
     const int64_t r_end = H.n;
-    auto row_of = [&](int it) -> int64_t {
-        const int64_t w = it / tile, t = it - w * tile;
-        return (w * gridDim.x + blockIdx.x) * (int64_t)tile * SLOTS + t * SLOTS + slot;
-    };
+    const int64_t cmask = H.C - 1;
+    // row of iteration it = (wave w, tile step t): advanced incrementally, so
+    // the loop carries no integer division
+    const int64_t wrap = wave_rows - (int64_t)(tile - 1) * SLOTS;
+    auto advance = [&](int64_t rr, int t) -> int64_t { return t + 1 == tile ? rr + wrap : rr + SLOTS; };
+    int64_t r = (int64_t)blockIdx.x * tile * SLOTS + slot;
+    int t_in_tile = 0;
 
     // Fixed-width path: the next row's entries are prefetched into (nc, nv).
     int32_t nc[EPL];
     V nv[EPL];
     auto load_entries = [&](int64_t rr) {
         const bool act = rr < r_end;
-        const int64_t k = rr / H.C;
-        const int64_t base = k * (int64_t)H.C * L + (rr - k * H.C);
+        const int64_t k = rr >> H.logC;
+        const int64_t base = (k << H.logC) * L + (rr & cmask);
 #pragma unroll
         for (int e = 0; e < EPL; ++e) {
             const int j = lane + e * G;
@@ -281,10 +285,10 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
             }
         }
     };
-    if constexpr (L > 0) load_entries(row_of(0));
+    if constexpr (L > 0) load_entries(r);
 
     for (int it = 0; it < iters; ++it) {
-        const int64_t r = row_of(it);
+        const int64_t r_next = advance(r, t_in_tile);
         const bool active = r < r_end;
         const int64_t orig = active ? (H.perm ? __ldg(H.perm + r) : r) : 0;
 
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
                 }
             }
             // prefetch the next row's entries while the gathers are in flight
-            load_entries(row_of(it + 1));
+            load_entries(r_next);
 #pragma unroll
             for (int e = 0; e < L; ++e) {
                 const V vj = shfl_val<R, CPLX>(mv[e / G], e % G, G);
@@ -361,8 +365,8 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
             int64_t base = 0;
             int len = 0;
             if (active) {
-                const int64_t k = r / H.C;
-                base = __ldg(H.chunk_ptr + k) + (r - k * H.C);
+                const int64_t k = r >> H.logC;
+                base = __ldg(H.chunk_ptr + k) + (r & cmask);
                 len = __ldg(H.chunk_len + k);
             }
             const int maxlen = __reduce_max_sync(FULL, len);
@@ -444,6 +448,8 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(R) == 4 ? 3 : 2)
                 }
             }
         }
+        r = r_next;
+        t_in_tile = t_in_tile + 1 == tile ? 0 : t_in_tile + 1;
     }
 
     if (!dots) return;

@@ -1,6 +1,7 @@
 // Device-side matrix construction: lattice Hamiltonian generators (CSR) and
 // the SELL-C-sigma build (Sec. 4; format of Kreutzer et al. 2014).
 #include <cub/cub.cuh>
+#include <cstdlib>
 
 #include "common.cuh"
 
@@ -223,6 +224,14 @@ __global__ void sell_fill_kernel(const int64_t* rowptr, const int32_t* ccol, con
     }
 }
 
+__global__ void to_df_values_kernel(const double* v, float2* d, int64_t count) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const float hi = __double2float_rn(v[t]);
+        d[t] = make_float2(hi, __double2float_rn(v[t] - (double)hi));
+    }
+}
+
 __global__ void to_single_kernel(const double* in, float* out, int64_t count) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -234,6 +243,79 @@ int grid_for(int64_t work, int threads = 256) {
     if (g < 1) g = 1;
     if (g > 65535 * 16) g = 65535 * 16;
     return (int)g;
+}
+
+// ------------------------------------------------------------ blocked ELL copy
+
+// Block columns of block row br other than br itself, ascending and distinct,
+// into list[0 .. kBellLB-2]; returns their count, or kBellLB when there are
+// more than kBellLB - 1 (the matrix then gets no blocked copy).
+__device__ int bell_collect(const int64_t* rowptr, const int32_t* ccol, int64_t br,
+                            int32_t* list) {
+    int cnt = 0;
+    for (int r = 0; r < kBellB; ++r) {
+        const int64_t row = br * kBellB + r;
+        for (int64_t p = rowptr[row]; p < rowptr[row + 1]; ++p) {
+            const int32_t bc = ccol[p] / kBellB;
+            if (bc == br) continue;
+            int i = 0;
+            while (i < cnt && list[i] < bc) ++i;
+            if (i < cnt && list[i] == bc) continue;
+            if (cnt == kBellLB - 1) return kBellLB;
+            for (int j = cnt; j > i; --j) list[j] = list[j - 1];
+            list[i] = bc;
+            ++cnt;
+        }
+    }
+    return cnt;
+}
+
+__global__ void bell_check_kernel(const int64_t* rowptr, const int32_t* ccol, int64_t nbr,
+                                  int* too_many) {
+    for (int64_t br = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; br < nbr;
+         br += (int64_t)gridDim.x * blockDim.x) {
+        int32_t list[kBellLB];
+        if (bell_collect(rowptr, ccol, br, list) >= kBellLB) atomicOr(too_many, 1);
+    }
+}
+
+// Slot 0 holds the diagonal block, slots 1.. the other block columns in
+// ascending order, unused slots the diagonal block again with zero values.
+// Repeated (row, column) entries are summed in FP64 before rounding.
+__global__ void bell_fill_kernel(const int64_t* rowptr, const int32_t* ccol, const double* cval,
+                                 int64_t nbr, int32_t* bcol, float2* bval) {
+    for (int64_t br = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; br < nbr;
+         br += (int64_t)gridDim.x * blockDim.x) {
+        int32_t list[kBellLB];
+        const int cnt = bell_collect(rowptr, ccol, br, list);
+        int32_t cols[kBellLB];
+        cols[0] = (int32_t)br;
+        for (int k = 1; k < kBellLB; ++k) cols[k] = k - 1 < cnt ? list[k - 1] : (int32_t)br;
+        double2 acc[kBellLB][kBellB * kBellB];
+        for (int k = 0; k < kBellLB; ++k)
+            for (int e = 0; e < kBellB * kBellB; ++e) acc[k][e] = make_double2(0.0, 0.0);
+        for (int r = 0; r < kBellB; ++r) {
+            const int64_t row = br * kBellB + r;
+            for (int64_t p = rowptr[row]; p < rowptr[row + 1]; ++p) {
+                const int32_t c = ccol[p];
+                const int32_t bc = c / kBellB;
+                int k = 0;
+                if (bc != br)
+                    for (k = 1; k < kBellLB && cols[k] != bc; ++k) {
+                    }
+                if (k == kBellLB) continue;  // not reached: every block column was collected
+                double2& a = acc[k][r * kBellB + (c - bc * kBellB)];
+                a.x += cval[2 * p];
+                a.y += cval[2 * p + 1];
+            }
+        }
+        for (int k = 0; k < kBellLB; ++k) {
+            bcol[br * kBellLB + k] = cols[k];
+            for (int e = 0; e < kBellB * kBellB; ++e)
+                bval[(br * kBellLB + k) * (kBellB * kBellB) + e] =
+                    make_float2(__double2float_rn(acc[k][e].x), __double2float_rn(acc[k][e].y));
+        }
+    }
 }
 
 }  // namespace
@@ -380,9 +462,43 @@ void build_sell_from_device_csr(Matrix& M, const int64_t* rowptr, const int32_t*
         to_single_kernel<<<grid_for(count), 256, 0, stream>>>((const double*)M.val64,
                                                               (float*)M.val32, count);
         CHEBFD_CHECK_CUDA(cudaGetLastError());
+        // double-float copy: each FP64 value v -> (hi, lo) = (fl32(v), fl32(v - hi))
+        CHEBFD_CHECK_CUDA(cudaMalloc(&M.valdf, std::max<int64_t>(count, 1) * 2 * sizeof(float)));
+        to_df_values_kernel<<<grid_for(count), 256, 0, stream>>>((const double*)M.val64,
+                                                                (float2*)M.valdf, count);
+        CHEBFD_CHECK_CUDA(cudaGetLastError());
     }
     CHEBFD_CHECK_CUDA(cudaStreamSynchronize(stream));
     cudaFree(len);
+    if (also_single && M.complex_values && M.identity_perm && n % kBellB == 0) {
+        const char* e = getenv("CHEBFD_BLOCKED");
+        if (!(e && e[0] == '0')) build_bell(M, rowptr, ccol, (const double*)cval, stream);
+    }
+}
+
+void build_bell(Matrix& M, const int64_t* rowptr, const int32_t* ccol, const double* cval,
+                cudaStream_t stream) {
+    const int64_t nbr = M.n / kBellB;
+    // dense blocks may store at most 4x the entries they replace
+    if (nbr == 0 || (double)kBellLB * kBellB * kBellB > 4.0 * (double)M.nnz / (double)nbr) return;
+    int* flag = nullptr;
+    CHEBFD_CHECK_CUDA(cudaMalloc(&flag, sizeof(int)));
+    CHEBFD_CHECK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), stream));
+    bell_check_kernel<<<grid_for(nbr), 256, 0, stream>>>(rowptr, ccol, nbr, flag);
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+    int too_many = 0;
+    CHEBFD_CHECK_CUDA(cudaMemcpyAsync(&too_many, flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CHEBFD_CHECK_CUDA(cudaStreamSynchronize(stream));
+    cudaFree(flag);
+    if (too_many) return;
+    CHEBFD_CHECK_CUDA(cudaMalloc(&M.bell_col, nbr * kBellLB * sizeof(int32_t)));
+    CHEBFD_CHECK_CUDA(
+        cudaMalloc(&M.bell_val32, nbr * kBellLB * kBellB * kBellB * sizeof(float2)));
+    bell_fill_kernel<<<grid_for(nbr, 128), 128, 0, stream>>>(rowptr, ccol, cval, nbr, M.bell_col,
+                                                            (float2*)M.bell_val32);
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+    CHEBFD_CHECK_CUDA(cudaStreamSynchronize(stream));
+    M.bell_enabled = true;
 }
 
 }  // namespace chebfd

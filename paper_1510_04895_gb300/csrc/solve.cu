@@ -9,6 +9,9 @@
 
 namespace chebfd {
 
+void filter_block_df_impl(const Matrix& M, double alpha, double beta, const double* gc, int Np,
+                          void* X, int64_t ld, int nb, cudaStream_t s);
+
 void filter_block_impl(const Matrix& M, double alpha, double beta, const double* gc, int Np,
                        void* X, int64_t ld, int nb, chebfd_dtype dt, double* moments,
                        cudaStream_t s, int panel = 0);
@@ -88,7 +91,11 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
     const bool cplx = M.complex_values;
     const chebfd_dtype d64 = cplx ? CHEBFD_C128 : CHEBFD_R64;
     const chebfd_dtype d32 = cplx ? CHEBFD_C64 : CHEBFD_R32;
-    const bool mixed = p.precision == CHEBFD_PRECISION_MIXED;
+    CHEBFD_REQUIRE(p.precision >= CHEBFD_PRECISION_FP64 &&
+                       p.precision <= CHEBFD_PRECISION_MIXED_DF,
+                   CHEBFD_EINVAL, "unknown precision");
+    const bool df = p.precision == CHEBFD_PRECISION_MIXED_DF;
+    const bool mixed = p.precision == CHEBFD_PRECISION_MIXED || df;
     CHEBFD_REQUIRE(!mixed || M.val32 != nullptr, CHEBFD_EINVAL,
                    "mixed precision needs a matrix built with also_single");
     if (p.nb <= 0) p.nb = cplx ? 64 : 128;
@@ -123,7 +130,11 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
             filter_block_impl(M, alpha, beta, gc.data(), p.Np, X32.p, ld, ns, d32, nullptr, s, p.nb);
             convert_block_impl(X32.p, d32, ld, Y64.p, d64, ld, n, ns, s);
         } else {
-            filter_block_impl(M, alpha, beta, gc.data(), p.Np, Y64.p, ld, ns, d64, nullptr, s, p.nb);
+            if (df)
+                filter_block_df_impl(M, alpha, beta, gc.data(), p.Np, Y64.p, ld, ns, s);
+            else
+                filter_block_impl(M, alpha, beta, gc.data(), p.Np, Y64.p, ld, ns, d64, nullptr,
+                                  s, p.nb);
             ++fp64_its;
         }
         CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));

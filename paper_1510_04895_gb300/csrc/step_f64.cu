@@ -8,18 +8,11 @@ namespace chebfd {
 
 namespace {
 
-// Resident blocks per SM of one instantiation (occupancy API, cached), capped
-// by CHEBFD_STEP_BPS when set: the persistent grid is whole waves.
+// Resident blocks per SM of one instantiation (occupancy API, cached per
+// kernel), capped by CHEBFD_STEP_BPS when set: the persistent grid is whole waves.
 template <class Kern>
 int blocks_per_sm(Kern kern, size_t smem) {
-    static int cached[2] = {0, 0};
-    int& occ = cached[smem ? 1 : 0];
-    if (!occ) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, STEP_THREADS, smem) !=
-                cudaSuccess || occ < 1)
-            occ = 1;
-    }
-    int b = occ;
+    int b = cached_occupancy(reinterpret_cast<const void*>(kern), STEP_THREADS, smem);
     if (const char* e = getenv("CHEBFD_STEP_BPS")) b = std::max(1, std::min(b, atoi(e)));
     return std::min(b, 8);
 }

@@ -17,9 +17,12 @@ TOPI_SMALL = dict(kind="topi", Lx=8, Ly=8, Lz=8, t=1.0, m=1.0, W=0.5, seed=0,
 TOPI_MEDIUM = dict(kind="topi", Lx=64, Ly=64, Lz=32, t=1.0, m=1.0, W=1.0, seed=1,
                    ns=256, nb=64, kernel="lanczos")
 
-# Disordered graphene, 1024 x 1024 cells (N = 2097152), 4 stored entries per row.
-GRAPHENE = dict(kind="graphene", Lx=1024, Ly=1024, t=1.0, W=1.0, seed=2, ns=512, nb=64,
-                kernel="lanczos")
+# Disordered graphene, 1024 x 1024 cells (N = 2097152), 4 stored entries per
+# row, onsite disorder in [-0.5, 0.5]; central window with about 200
+# eigenpairs (tests/golden/graphene_1024x1024_window.txt), n_s = 512 filtered
+# in four blocks of 128.
+GRAPHENE = dict(kind="graphene", Lx=1024, Ly=1024, Lz=1, t=1.0, m=0.0, W=1.0, seed=2, ns=512,
+                nb=128, kernel="lanczos")
 
 # Large insulator, 200x200x100 x 4 (N = 16e6), complex64 filter, 4 chunks of 64.
 TOPI_LARGE = dict(kind="topi", Lx=200, Ly=200, Lz=100, t=1.0, m=1.0, W=0.5, seed=3,

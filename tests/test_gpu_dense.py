@@ -90,7 +90,7 @@ def _dense_window(Ho, lo, hi):
     return e[(e >= lo) & (e <= hi)], e
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_df"])
 def test_solve_smallest_insulator_against_dense(precision):
     """8x8x8x4 insulator (N = 2048), W = 0.5, window [-0.1, 0.1], n_s = 64,
     N_p = 200, Jackson: all window eigenvalues within 1e-10 ||H|| of the dense
@@ -110,17 +110,18 @@ def test_solve_smallest_insulator_against_dense(precision):
     assert np.abs(orr.residual_norms(Ho, V, r["lam"])).max() <= 1e-9 * normH
     th = np.sort(r["lam"])
     assert np.abs(th + th[::-1]).max() <= 1e-10 * normH
-    if precision == "mixed":
+    if precision != "fp64":
         assert 1 <= r["fp64_iterations"] < r["iterations"]
     # the oracle run on the same workload finds the same eigenvalues
     ro = osolve.chebfd(Ho, r["a"], r["b"], -0.1, 0.1, 64, 200, 1e-9, kind="jackson", seed=0)
     assert np.abs(np.sort(ro["theta"]) - th).max() <= 1e-10 * normH
 
 
-def test_solve_graphene_real_against_dense():
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df"])
+def test_solve_graphene_real_against_dense(precision):
     H = pkg.chebfd_matrix_create_lattice("graphene", 40, 36, W=1.0, seed=2, also_single=True)
     Ho = lattice.to_scipy(*lattice.graphene_csr(40, 36, W=1.0, seed=2))
-    r = pkg.chebfd_solve(H, -0.05, 0.05, 48, 400, eps=1e-9, kernel="lanczos", precision="mixed")
+    r = pkg.chebfd_solve(H, -0.05, 0.05, 48, 400, eps=1e-9, kernel="lanczos", precision=precision)
     ew, _ = _dense_window(Ho, -0.05, 0.05)
     normH = max(abs(r["a"]), abs(r["b"]))
     assert r["converged"] and r["nev"] == len(ew) > 0
