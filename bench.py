@@ -297,32 +297,43 @@ def bench_ensemble(pkg, workloads, dev, peak_gbs):
 def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chiral=True):
     """Wall time of the whole ChebFD solve (Sec. 3.1 steps 4-8) to residual
     <= eps ||H|| for every accepted pair in [-delta, delta]: plain FP64 against
-    the mixed form (single-precision filter until the residuals stall, then
-    FP64 sweeps; FP64 Gram, Rayleigh-Ritz and residuals throughout)."""
+    the mixed forms (single-precision filter until the residuals stall, then
+    FP64 or double-float sweeps; FP64 Gram, Rayleigh-Ritz and residuals
+    throughout), and the mixed double-float form with the MLP's parameters."""
     import torch
     out = {}
     lams = {}
-    for prec in ("fp64", "mixed"):
+
+    def run(name, ns_r, Np_r, kern, prec, extra=None, t_pre=0.0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = pkg.chebfd_solve(H, -delta, delta, ns, Np, eps=eps, kernel="lanczos", precision=prec,
+        r = pkg.chebfd_solve(H, -delta, delta, ns_r, Np_r, eps=eps, kernel=kern, precision=prec,
                              a=a, b=b, max_iter=40, seed=0)
         torch.cuda.synchronize()
-        t = time.perf_counter() - t0
+        t = time.perf_counter() - t0 + t_pre
         normH = max(abs(r["a"]), abs(r["b"]))
         lam = np.sort(r["lam"])
-        lams[prec] = lam
-        out[prec] = {"seconds": t, "iterations": r["iterations"],
-                     "fp64_filter_iterations": r["fp64_iterations"], "nev": r["nev"],
-                     "converged": r["converged"], "max_residual_over_normH":
-                         float(r["res"].max() / normH) if r["nev"] else None,
-                     "seconds_filter": r["seconds_filter"], "seconds_dense": r["seconds_dense"],
-                     "n_mvm": r["n_mvm"]}
+        lams[name] = lam
+        out[name] = dict(extra or {})
+        out[name].update({"seconds": t, "precision": prec, "iterations": r["iterations"],
+                          "fp64_filter_iterations": r["fp64_iterations"], "nev": r["nev"],
+                          "converged": r["converged"], "max_residual_over_normH":
+                              float(r["res"].max() / normH) if r["nev"] else None,
+                          "seconds_filter": r["seconds_filter"],
+                          "seconds_dense": r["seconds_dense"], "n_mvm": r["n_mvm"]})
         if chiral and r["nev"]:
             # spec(H) = -spec(H) for the insulator: the window set is +- paired
-            out[prec]["chiral_pairing_error"] = float(np.abs(lam + lam[::-1]).max())
+            out[name]["chiral_pairing_error"] = float(np.abs(lam + lam[::-1]).max())
+        if name != "fp64" and len(lam) == len(lams["fp64"]) and len(lam):
+            out[name]["max_eigenvalue_difference_vs_fp64"] = float(
+                np.abs(lam - lams["fp64"]).max())
+        if name != "fp64":
+            out["speedup_%s_over_fp64" % name] = out["fp64"]["seconds"] / t
+
+    for prec in ("fp64", "mixed", "mixed_df"):
+        run(prec, ns, Np, "lanczos", prec)
     # learned parameters: (N_p, n_s, kernel) from the trained MLP on the KPM
-    # features of this matrix and window, with the mixed-precision solve
+    # features of this matrix and window (its time is part of the solve's)
     wpath = os.path.join(ROOT, "paper_1510_04895_gb300", "data", "mlp_weights.npy")
     if learned and os.path.exists(wpath):
         from paper_1510_04895_gb300 import mlp_train
@@ -333,27 +344,10 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chir
         ns_m, Np_m, kern_m, nt = pkg.chebfd_choose_params(H, -delta, delta, mlp=net, a=a, b=b,
                                                           m_feat=mlp_train.M_FEAT)
         ns_m = max(ns_m, int(np.ceil(nt / 4.0)) * 4 + 8)   # never fewer vectors than targets
-        r = pkg.chebfd_solve(H, -delta, delta, ns_m, Np_m, eps=eps, kernel=kern_m,
-                             precision="mixed", a=a, b=b, max_iter=40, seed=0)
-        torch.cuda.synchronize()
-        t = time.perf_counter() - t0
-        normH = max(abs(r["a"]), abs(r["b"]))
-        lam = np.sort(r["lam"])
-        out["mixed_mlp"] = {"seconds": t, "ns": ns_m, "Np": Np_m, "kernel": kern_m,
-                            "kpm_n_target": nt, "iterations": r["iterations"],
-                            "fp64_filter_iterations": r["fp64_iterations"], "nev": r["nev"],
-                            "converged": r["converged"],
-                            "max_residual_over_normH": float(r["res"].max() / normH)
-                            if r["nev"] else None,
-                            "seconds_filter": r["seconds_filter"],
-                            "seconds_dense": r["seconds_dense"]}
-        if len(lam) == len(lams["fp64"]) and len(lam):
-            out["mixed_mlp"]["max_eigenvalue_difference_vs_fp64"] = float(
-                np.abs(lam - lams["fp64"]).max())
-        out["speedup_mixed_mlp_over_fp64"] = out["fp64"]["seconds"] / t
-    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
-    if len(lams["fp64"]) == len(lams["mixed"]) and len(lams["fp64"]):
-        out["max_eigenvalue_difference"] = float(np.abs(lams["fp64"] - lams["mixed"]).max())
+        t_choose = time.perf_counter() - t0
+        run("mixed_df_mlp", ns_m, Np_m, kern_m, "mixed_df",
+            extra={"ns": ns_m, "Np": Np_m, "kernel": kern_m, "kpm_n_target": nt,
+                   "seconds_parameter_choice": t_choose}, t_pre=t_choose)
     out["eps"] = eps
     out["workload"] = "%s, window [-%.6g, %.6g], n_s = %d, N_p = %d, Lanczos mu=2" % (
         label, delta, delta, ns, Np)

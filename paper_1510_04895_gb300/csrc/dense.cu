@@ -66,8 +66,10 @@ struct Buf {
     Buf(size_t bytes, cudaStream_t st) : s(st) {
         if (bytes) CHEBFD_CHECK_CUDA(cudaMallocAsync(&p, bytes, st));
     }
-    ~Buf() {
+    ~Buf() { reset(); }
+    void reset() {
         if (p) cudaFreeAsync(p, s);
+        p = nullptr;
     }
     Buf(const Buf&) = delete;
     Buf& operator=(const Buf&) = delete;
@@ -446,6 +448,131 @@ void rayleigh_ritz_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dt
         CHEBFD_CHECK_CUDA(cudaMemcpyAsync(res_host, res.p, ns * sizeof(double),
                                           cudaMemcpyDeviceToHost, s));
     CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+namespace {
+
+// C (ns x ns, column-major) = op(A) * B, op = conjugate transpose if ah.
+void gemm_small(Handles& h, bool cplx, bool ah, int ns, const double* A, const double* B,
+                double* C) {
+    if (cplx) {
+        const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0),
+                              zero = make_cuDoubleComplex(0.0, 0.0);
+        CHEBFD_CHECK_CUBLAS(cublasZgemm(h.blas, ah ? CUBLAS_OP_C : CUBLAS_OP_N, CUBLAS_OP_N, ns,
+                                        ns, ns, &one, (const cuDoubleComplex*)A, ns,
+                                        (const cuDoubleComplex*)B, ns, &zero,
+                                        (cuDoubleComplex*)C, ns));
+    } else {
+        const double one = 1.0, zero = 0.0;
+        CHEBFD_CHECK_CUBLAS(cublasDgemm(h.blas, ah ? CUBLAS_OP_T : CUBLAS_OP_N, CUBLAS_OP_N, ns,
+                                        ns, ns, &one, A, ns, B, ns, &zero, C, ns));
+    }
+}
+
+}  // namespace
+
+// Steps 6-7 of Sec. 3.1 in one pass over the dense work: two SVQB passes and
+// the Rayleigh-Ritz projection, with the second SVQB transform folded into
+// the projection instead of applied to the block.  With Y1 = Y T1 (pass 1,
+// refill as in orthonormalize_impl), the second transform T2 comes from
+// Y1^H Y1, and Y2 = Y1 T2 is never formed: Y2^H H Y2 = T2^H (Y1^H H Y1) T2 is
+// an n_s x n_s product, and the Ritz vectors and their products with H are
+// V = Y1 (T2 S), HV = (H Y1)(T2 S).  Tall products: three Gram-type GEMMs
+// (Y^H Y, Y1^H Y1, Y1^H H Y1) and three block GEMMs (Y T1, V, HV) instead of
+// the five + three of the separate calls.  A rank drop in the second pass
+// falls back to the separate calls.  Y <- Ritz vectors (ascending theta).
+void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype dt, uint64_t seed,
+                   int64_t* refill_counter, double* theta_host, double* res_host,
+                   cudaStream_t s) {
+    check_fp64_block(dt, Yv, M.n, ns, ld);
+    const bool cplx = dt == CHEBFD_C128;
+    CHEBFD_REQUIRE(cplx == M.complex_values, CHEBFD_EINVAL, "dtype does not match the matrix");
+    const size_t es = cplx ? 16 : 8;
+    const int64_t n = M.n;
+    double* Y = (double*)Yv;
+    Handles& h = handles_for_current_device(s);
+    Buf S((size_t)ns * ns * es, s), d((size_t)ns * sizeof(double), s),
+        th((size_t)ns * sizeof(double), s), Mt((size_t)ns * ns * es, s),
+        T((size_t)n * ld * es, s);
+    std::vector<double> hth(ns);
+    int64_t counter = refill_counter ? *refill_counter : 0;
+
+    // SVQB pass on the block B (already Gram'ed into S): scale, eigensolve,
+    // transform columns; returns the rank kept.
+    auto svqb_transform = [&]() -> int {
+        if (cplx)
+            diag_scale_kernel<true><<<1, 1024, 0, s>>>(S.as<double>(), ns, d.as<double>());
+        else
+            diag_scale_kernel<false><<<1, 1024, 0, s>>>(S.as<double>(), ns, d.as<double>());
+        heev(h, cplx, S.as<double>(), ns, th.as<double>(), s);
+        CHEBFD_CHECK_CUDA(cudaMemcpyAsync(hth.data(), th.p, ns * sizeof(double),
+                                          cudaMemcpyDeviceToHost, s));
+        CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+        const double thr = ns * std::ldexp(1.0, -52) * hth[ns - 1];
+        int first = 0;
+        while (first < ns && !(hth[first] >= thr)) ++first;
+        const int r = ns - first;
+        CHEBFD_REQUIRE(r >= 1, CHEBFD_ENUMERIC, "orthonormalisation: block has rank 0");
+        if (cplx)
+            form_transform_kernel<true><<<grid1d((int64_t)ns * r), 256, 0, s>>>(
+                S.as<double>(), d.as<double>(), th.as<double>(), ns, first, r, Mt.as<double>());
+        else
+            form_transform_kernel<false><<<grid1d((int64_t)ns * r), 256, 0, s>>>(
+                S.as<double>(), d.as<double>(), th.as<double>(), ns, first, r, Mt.as<double>());
+        return r;
+    };
+
+    // ---- pass 1: Y1 = Y T1 (+ refill) into T
+    gram(h, cplx, Y, n, ns, ld, S.as<double>());
+    const int r1 = svqb_transform();
+    gemm_ch(h, cplx, r1, n, ns, Mt.as<double>(), ns, Y, ld, T.as<double>(), ld);
+    if (r1 < ns) {
+        if (cplx)
+            refill_kernel<true><<<grid1d(n * (ns - r1)), 256, 0, s>>>(T.as<double>(), n, ld, r1,
+                                                                      ns, counter, seed);
+        else
+            refill_kernel<false><<<grid1d(n * (ns - r1)), 256, 0, s>>>(T.as<double>(), n, ld, r1,
+                                                                       ns, counter, seed);
+        counter += ns - r1;
+    }
+    // ---- pass 2: T2 from Y1^H Y1, kept in Mt (stored conj(T2))
+    gram(h, cplx, T.as<double>(), n, ns, ld, S.as<double>());
+    const int r2 = svqb_transform();
+    if (r2 < ns) {
+        // rank drop after pass 1: the separate, up to three-pass path
+        copy_block(Y, ld, T.p, ld, n, ns, es, s);
+        T.reset();
+        if (refill_counter) *refill_counter = counter;
+        orthonormalize_impl(Y, n, ns, ld, dt, seed, refill_counter, nullptr, s);
+        rayleigh_ritz_impl(M, Y, ld, ns, dt, theta_host, res_host, nullptr, s);
+        return;
+    }
+    // ---- Rayleigh-Ritz in the basis Y2 = Y1 T2
+    Buf HY((size_t)n * ld * es, s), G((size_t)ns * ns * es, s), W2((size_t)ns * ns * es, s),
+        res((size_t)ns * sizeof(double), s);
+    spmv_impl(M, 1.0, 0.0, T.p, HY.p, ld, ns, dt, s);
+    gemm_nh(h, cplx, ns, n, HY.as<double>(), ld, T.as<double>(), ld, G.as<double>(), ns);
+    // stored conj(A2) = Mt^H conj(A1) Mt with conj(A1) in G
+    gemm_small(h, cplx, false, ns, G.as<double>(), Mt.as<double>(), W2.as<double>());
+    gemm_small(h, cplx, true, ns, Mt.as<double>(), W2.as<double>(), G.as<double>());
+    if (cplx)
+        hermitize_kernel<true><<<grid1d((int64_t)ns * ns), 256, 0, s>>>(G.as<double>(), ns);
+    else
+        hermitize_kernel<false><<<grid1d((int64_t)ns * ns), 256, 0, s>>>(G.as<double>(), ns);
+    heev(h, cplx, G.as<double>(), ns, th.as<double>(), s);
+    // C = Mt E (stored conj of T2 S); V = Y1 conj(C), HV = HY1 conj(C)
+    gemm_small(h, cplx, false, ns, Mt.as<double>(), G.as<double>(), W2.as<double>());
+    gemm_ch(h, cplx, ns, n, ns, W2.as<double>(), ns, T.as<double>(), ld, Y, ld);
+    gemm_ch(h, cplx, ns, n, ns, W2.as<double>(), ns, HY.as<double>(), ld, T.as<double>(), ld);
+    residuals_from_blocks(cplx, T.as<double>(), Y, th.as<double>(), n, ld, ns, res.as<double>(), s);
+    CHEBFD_CHECK_CUDA(cudaMemcpyAsync(theta_host, th.p, ns * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+    if (res_host)
+        CHEBFD_CHECK_CUDA(cudaMemcpyAsync(res_host, res.p, ns * sizeof(double),
+                                          cudaMemcpyDeviceToHost, s));
+    CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+    if (refill_counter) *refill_counter = counter;
 }
 
 void residuals_impl(const Matrix& M, const void* V, const double* theta_host, int64_t ld, int k,
