@@ -66,8 +66,9 @@ typedef enum chebfd_kernel {
 } chebfd_kernel;
 
 typedef enum chebfd_lattice_kind {
-    CHEBFD_LATTICE_TOPI = 0,     /* 3D topological insulator, Eq. Ham form (Sec. 5.1) */
-    CHEBFD_LATTICE_GRAPHENE = 1  /* 2D honeycomb lattice with onsite disorder (Sec. 5.4) */
+    CHEBFD_LATTICE_TOPI = 0,      /* 3D topological insulator, periodic (Sec. 5.1 pattern) */
+    CHEBFD_LATTICE_GRAPHENE = 1,  /* 2D honeycomb lattice with onsite disorder (Sec. 5.4) */
+    CHEBFD_LATTICE_TOPI_SLAB = 2  /* the paper's Eq. Ham: insulator slab, open in z */
 } chebfd_lattice_kind;
 
 /* Description of a generated lattice Hamiltonian.
@@ -76,6 +77,10 @@ typedef enum chebfd_lattice_kind {
  *    site s to s+e_j plus Hermitian conjugate, periodic; 13 entries per row
  *    (N_nzr = 13, Sec. 4).  Gamma1 = sz(x)s0, Gamma2 = sx(x)sx,
  *    Gamma3 = sx(x)sy, Gamma4 = sx(x)sz.
+ *  TOPI_SLAB: Eq. Ham of Sec. 5.1: the same hopping, onsite V_s Gamma0 +
+ *    m Gamma1 (Gamma0 = identity; the paper has m = 2), periodic in x and y and
+ *    open in z (a slab of Lz layers): 11 entries in the rows of the two
+ *    surface layers, 13 elsewhere.  Onsite values V_s + m and V_s - m.
  *  GRAPHENE: Lx*Ly cells, row = 2*(i + Lx*j) + sublattice, hopping -t to the
  *    three nearest neighbours, onsite V; 4 entries per row (N_nzr = 4, Sec. 4).
  *    Lz and m are ignored.

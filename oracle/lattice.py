@@ -6,8 +6,11 @@
   (row of s + e_j, column of s) plus its Hermitian conjugate at the transposed
   position; periodic in all three axes; 4 orbitals per site; row = 4 s + o with
   s = x + Lx (y + Ly z).  This gives the 13 stored entries per row quoted in
-  Sec. 4 (N_nzr = 13).  The paper's own onsite term V_n Gamma^0 + 2 Gamma^1 is
-  the same sparsity pattern with other onsite values (not generated here).
+  Sec. 4 (N_nzr = 13).
+* The paper's own form of Eq. Ham (`topi_slab_csr`): the same hopping, onsite
+  V_n Gamma^0 + m Gamma^1 with Gamma^0 the identity (m = 2 in Sec. 5.1), on a
+  slab that is periodic in x and y and open in z (the surface layers have no
+  z neighbour outside the slab: 11 entries in their rows).
 * Graphene (Sec. 5.4, Tab. benchmark): honeycomb lattice, hopping -t between
   nearest neighbours, onsite disorder; 4 stored entries per row with the
   diagonal (N_nzr = 4 in Sec. 4).
@@ -113,6 +116,75 @@ def topi_csr(Lx, Ly, Lz, t=1.0, m=1.0, W=0.0, seed=0):
     rows = np.concatenate(rows); cols = np.concatenate(cols)
     vals = np.concatenate(vals); order = np.concatenate(order)
     return _merge(rows, cols, vals, order, n, np.complex128)
+
+
+def topi_slab_csr(Lx, Ly, Lz, t=1.0, m=2.0, W=0.0, seed=0):
+    """CSR of Eq. Ham on an Lx x Ly x Lz slab (periodic in x, y; open in z):
+    onsite V_s + m Gamma1[o][o] on the diagonal, hopping as in topi_csr."""
+    nsite = Lx * Ly * Lz
+    n = 4 * nsite
+    s = np.arange(nsite, dtype=np.int64)
+    x = s % Lx
+    y = (s // Lx) % Ly
+    z = s // (Lx * Ly)
+    V = disorder(seed, nsite, W)
+    h = t / 2.0
+    rows, cols, vals, order = [], [], [], []
+    g1 = np.real(np.diag(GAMMA[0]))
+    for o in range(4):
+        r = 4 * s + o
+        rows.append(r); cols.append(4 * s + o)
+        vals.append((V + m * g1[o]).astype(np.complex128))   # one rounding: V + m or V - m
+        order.append(np.zeros(nsite, dtype=np.int64))
+        rank = 1
+        for j in range(3):
+            G = GAMMA[j + 1]
+            p = int(np.nonzero(G[o])[0][0])
+            for sign in (+1, -1):
+                keep = np.ones(nsite, dtype=bool)
+                cx, cy, cz = x.copy(), y.copy(), z.copy()
+                if j == 0:
+                    cx = (x + sign) % Lx
+                elif j == 1:
+                    cy = (y + sign) % Ly
+                else:
+                    cz = z + sign
+                    keep = (cz >= 0) & (cz < Lz)
+                sn = (cx + Lx * (cy + Ly * cz))[keep]
+                k = int(keep.sum())
+                dval = -h * g1[o]
+                q = 1.0 if sign < 0 else -1.0
+                off = complex(-q * h * G[o, p].imag + 0.0, q * h * G[o, p].real + 0.0)
+                rows.append(r[keep]); cols.append(4 * sn + o)
+                vals.append(np.full(k, dval, dtype=np.complex128))
+                order.append(np.full(k, rank, dtype=np.int64)); rank += 1
+                rows.append(r[keep]); cols.append(4 * sn + p)
+                vals.append(np.full(k, off, dtype=np.complex128))
+                order.append(np.full(k, rank, dtype=np.int64)); rank += 1
+    rows = np.concatenate(rows); cols = np.concatenate(cols)
+    vals = np.concatenate(vals); order = np.concatenate(order)
+    return _merge(rows, cols, vals, order, n, np.complex128)
+
+
+def topi_slab_clean_spectrum(Lx, Ly, Lz, t=1.0, m=2.0):
+    """Eigenvalues of the clean slab from Bloch's theorem in x and y: for each
+    (k_x, k_y) the 4 Lz x 4 Lz chain with layer block (m - t cos k_x - t cos k_y)
+    Gamma1 + t sin k_x Gamma2 + t sin k_y Gamma3 and layer coupling
+    -t (Gamma1 - i Gamma4)/2 from layer z to z+1 (plus Hermitian conjugate)."""
+    A = -t * (GAMMA[0] - 1j * GAMMA[3]) / 2.0
+    out = []
+    for kx in 2 * np.pi * np.arange(Lx) / Lx:
+        for ky in 2 * np.pi * np.arange(Ly) / Ly:
+            D = ((m - t * np.cos(kx) - t * np.cos(ky)) * GAMMA[0]
+                 + t * np.sin(kx) * GAMMA[1] + t * np.sin(ky) * GAMMA[2])
+            Hk = np.zeros((4 * Lz, 4 * Lz), dtype=np.complex128)
+            for zz in range(Lz):
+                Hk[4 * zz:4 * zz + 4, 4 * zz:4 * zz + 4] = D
+                if zz + 1 < Lz:
+                    Hk[4 * (zz + 1):4 * (zz + 1) + 4, 4 * zz:4 * zz + 4] = A
+                    Hk[4 * zz:4 * zz + 4, 4 * (zz + 1):4 * (zz + 1) + 4] = A.conj().T
+            out.append(np.linalg.eigvalsh(Hk))
+    return np.sort(np.concatenate(out))
 
 
 def graphene_csr(Lx, Ly, t=1.0, W=0.0, seed=0):

@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(HERE, "libchebfd.so")
 
 R64, C128, R32, C64 = 0, 1, 2, 3
 KERNEL_NONE, KERNEL_FEJER, KERNEL_JACKSON, KERNEL_LANCZOS = 0, 1, 2, 3
-LATTICE_TOPI, LATTICE_GRAPHENE = 0, 1
+LATTICE_TOPI, LATTICE_GRAPHENE, LATTICE_TOPI_SLAB = 0, 1, 2
+LATTICES = {"topi": LATTICE_TOPI, "graphene": LATTICE_GRAPHENE, "topi_slab": LATTICE_TOPI_SLAB}
 KERNEL_IDS = {"none": KERNEL_NONE, "fejer": KERNEL_FEJER, "jackson": KERNEL_JACKSON,
               "lanczos": KERNEL_LANCZOS}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "ENOCONV",
@@ -272,7 +273,7 @@ def chebfd_matrix_create_csr(rowptr, col, val, sell_C=1, sell_sigma=1, also_sing
 
 def chebfd_matrix_create_lattice(kind, Lx, Ly, Lz=1, t=1.0, m=1.0, W=0.0, seed=0, sell_C=1,
                                  sell_sigma=1, also_single=False, stream=None):
-    d = LatticeDesc(kind=LATTICE_TOPI if kind in ("topi", LATTICE_TOPI) else LATTICE_GRAPHENE,
+    d = LatticeDesc(kind=LATTICES[kind] if isinstance(kind, str) else int(kind),
                     Lx=Lx, Ly=Ly, Lz=Lz, t=t, m=m, W=W, seed=seed, sell_C=sell_C,
                     sell_sigma=sell_sigma, also_single=1 if also_single else 0, reserved=0)
     h = c_vp()

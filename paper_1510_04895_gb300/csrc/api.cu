@@ -463,7 +463,7 @@ chebfd_status chebfd_matrix_create_lattice(const chebfd_lattice_desc* desc, void
             int64_t n = 0;
             generate_lattice_csr(*desc, &n, &d_rowptr, &d_col, &d_val, s);
             M.n = n;
-            M.complex_values = desc->kind == CHEBFD_LATTICE_TOPI;
+            M.complex_values = desc->kind != CHEBFD_LATTICE_GRAPHENE;
             build_sell_from_device_csr(M, d_rowptr, d_col, d_val, desc->sell_C,
                                        desc->sell_sigma, desc->also_single != 0, s);
         } catch (...) {

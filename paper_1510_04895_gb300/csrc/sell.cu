@@ -31,11 +31,17 @@ __device__ int topi_contributions(int64_t row, const LatticeParams& P, Entry* e)
     const int64_t x = s % P.Lx, y = (s / P.Lx) % P.Ly, z = s / (P.Lx * P.Ly);
     const double u = splitmix_uniform(P.seed, STREAM_DISORDER, (uint64_t)s);
     const double V = __dmul_rn(P.W, u - 0.5);
-    const double mv = __dadd_rn(P.m, V);
     const double h = P.t / 2.0;
     const bool upper = o < 2;  // Gamma1 = diag(1, 1, -1, -1)
+    const bool slab = P.kind == CHEBFD_LATTICE_TOPI_SLAB;
+    // onsite: (m + V_s) Gamma1, or for the slab V_s Gamma0 + m Gamma1 (Eq. Ham)
+    double onsite;
+    if (slab)
+        onsite = upper ? __dadd_rn(V, P.m) : __dadd_rn(V, -P.m);
+    else
+        onsite = upper ? __dadd_rn(P.m, V) : -__dadd_rn(P.m, V);
     int c = 0;
-    e[c++] = Entry{4 * s + o, upper ? mv : -mv, 0.0, 0};
+    e[c++] = Entry{4 * s + o, onsite, 0.0, 0};
     int rank = 1;
     for (int j = 0; j < 3; ++j) {
         // Off-diagonal partner p of Gamma_{j+1} and the entry Gamma_{j+1}[o][p].
@@ -56,7 +62,10 @@ __device__ int topi_contributions(int64_t row, const LatticeParams& P, Entry* e)
             int64_t cx = x, cy = y, cz = z;
             if (j == 0) cx = (x + sign + P.Lx) % P.Lx;
             if (j == 1) cy = (y + sign + P.Ly) % P.Ly;
-            if (j == 2) cz = (z + sign + P.Lz) % P.Lz;
+            if (j == 2) {
+                if (slab && (z + sign < 0 || z + sign >= P.Lz)) continue;  // open in z
+                cz = (z + sign + P.Lz) % P.Lz;
+            }
             const int64_t sn = cx + P.Lx * (cy + P.Ly * cz);
             const double dval = upper ? -h : h;  // -h * Gamma1[o][o]
             const double q = sign < 0 ? 1.0 : -1.0;  // T_j at s-e_j, T_j^dagger at s+e_j
@@ -93,8 +102,8 @@ __device__ int graphene_contributions(int64_t row, const LatticeParams& P, Entry
 
 // Stable sort by column, then merge equal columns summing left to right.
 __device__ int row_entries(int64_t row, const LatticeParams& P, Entry* e) {
-    int c = P.kind == CHEBFD_LATTICE_TOPI ? topi_contributions(row, P, e)
-                                          : graphene_contributions(row, P, e);
+    int c = P.kind == CHEBFD_LATTICE_GRAPHENE ? graphene_contributions(row, P, e)
+                                              : topi_contributions(row, P, e);
     for (int a = 1; a < c; ++a) {
         Entry v = e[a];
         int b = a - 1;
@@ -322,7 +331,8 @@ __global__ void bell_fill_kernel(const int64_t* rowptr, const int32_t* ccol, con
 
 void generate_lattice_csr(const chebfd_lattice_desc& d, int64_t* n_out, int64_t** d_rowptr,
                           int32_t** d_col, void** d_val, cudaStream_t stream) {
-    CHEBFD_REQUIRE(d.kind == CHEBFD_LATTICE_TOPI || d.kind == CHEBFD_LATTICE_GRAPHENE,
+    CHEBFD_REQUIRE(d.kind == CHEBFD_LATTICE_TOPI || d.kind == CHEBFD_LATTICE_GRAPHENE ||
+                       d.kind == CHEBFD_LATTICE_TOPI_SLAB,
                    CHEBFD_EINVAL, "unknown lattice kind");
     CHEBFD_REQUIRE(d.Lx >= 1 && d.Ly >= 1 && (d.kind == CHEBFD_LATTICE_GRAPHENE || d.Lz >= 1),
                    CHEBFD_EINVAL, "lattice edges must be >= 1");
@@ -331,14 +341,15 @@ void generate_lattice_csr(const chebfd_lattice_desc& d, int64_t* n_out, int64_t*
     P.kind = d.kind;
     P.Lx = d.Lx;
     P.Ly = d.Ly;
-    P.Lz = d.kind == CHEBFD_LATTICE_TOPI ? d.Lz : 1;
+    const bool topi = d.kind != CHEBFD_LATTICE_GRAPHENE;
+    P.Lz = topi ? d.Lz : 1;
     P.t = d.t;
     P.m = d.m;
     P.W = d.W;
     P.seed = d.seed;
-    const int64_t n = d.kind == CHEBFD_LATTICE_TOPI ? 4 * P.Lx * P.Ly * P.Lz : 2 * P.Lx * P.Ly;
+    const int64_t n = topi ? 4 * P.Lx * P.Ly * P.Lz : 2 * P.Lx * P.Ly;
     CHEBFD_REQUIRE(n < (1LL << 31), CHEBFD_EINVAL, "matrix dimension must be < 2^31");
-    const bool cplx = d.kind == CHEBFD_LATTICE_TOPI;
+    const bool cplx = topi;
     int64_t *rowptr = nullptr, *counts = nullptr;
     CHEBFD_CHECK_CUDA(cudaMalloc(&rowptr, (n + 1) * sizeof(int64_t)));
     CHEBFD_CHECK_CUDA(cudaMalloc(&counts, (n + 1) * sizeof(int64_t)));

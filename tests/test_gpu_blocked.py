@@ -111,3 +111,28 @@ def test_blocked_filter_full_size_insulator():
     bound = 6 * 30 * 2.0 ** -24 * np.linalg.norm(X0.cpu().numpy()) / np.linalg.norm(ref)
     assert rel(got[True], ref) <= bound
     assert rel(got[True], got[False]) <= bound
+
+
+@pytest.mark.parametrize("single", [True, False])
+def test_slab_filter_matches_oracle(single):
+    """Eq. Ham slab (open in z: 11-entry surface rows, so the blocked copy has
+    padded block columns and the SELL path its generic variable-width loop):
+    the filter within 1e-11 (FP64) or the FP32 bound (complex64) of the oracle."""
+    Lx, Ly, Lz = 6, 5, 4
+    H = pkg.chebfd_matrix_create_lattice("topi_slab", Lx, Ly, Lz, t=1.0, m=2.0, W=2.0, seed=3,
+                                         also_single=True)
+    assert H.blocked_width == 7
+    Ho = lattice.to_scipy(*lattice.topi_slab_csr(Lx, Ly, Lz, t=1.0, m=2.0, W=2.0, seed=3))
+    a, b = -5.5, 5.5
+    alpha, beta = coeffs.scaling(a, b)
+    gc = coeffs.filter_coeffs(a, b, -0.06, 0.06, 120, "lanczos")
+    X0 = workloads.random_block(4, H.n, 64, True)
+    X = torch.from_numpy(X0).to(DEV)
+    if single:
+        X = X.to(torch.complex64)
+    Xin = X.cpu().numpy().astype(np.complex128)
+    pkg.chebfd_filter_block(H, alpha, beta, gc, X)
+    ref = ofilt.filter_block(Ho, alpha, beta, gc, Xin)
+    err = rel(X.cpu().numpy(), ref)
+    tol = 120 * 30 * 2.0 ** -24 * np.linalg.norm(Xin) / np.linalg.norm(ref) if single else 1e-11
+    assert err <= tol, (err, tol)

@@ -27,6 +27,8 @@ def rel(a, b):
 def oracle_csr(kind, Lx, Ly, Lz=1, t=1.0, m=1.0, W=0.0, seed=0):
     if kind == "topi":
         return lattice.topi_csr(Lx, Ly, Lz, t=t, m=m, W=W, seed=seed)
+    if kind == "topi_slab":
+        return lattice.topi_slab_csr(Lx, Ly, Lz, t=t, m=m, W=W, seed=seed)
     return lattice.graphene_csr(Lx, Ly, t=t, W=W, seed=seed)
 
 
@@ -46,12 +48,15 @@ def assert_sell_equal(got, ref):
     ("topi", 8, 8, 8, 0.5, 0, 1, 1), ("topi", 3, 4, 5, 2.0, 7, 4, 1), ("topi", 2, 2, 3, 0.7, 3, 2, 1),
     ("topi", 2, 1, 3, 1.1, 9, 8, 16), ("graphene", 16, 12, 1, 1.0, 2, 1, 1),
     ("graphene", 2, 5, 1, 1.0, 4, 32, 64), ("graphene", 1, 3, 1, 0.3, 1, 4, 4),
+    ("topi_slab", 6, 5, 4, 2.0, 3, 1, 1), ("topi_slab", 2, 3, 1, 2.0, 5, 4, 8),
+    ("topi_slab", 3, 2, 7, 0.7, 1, 8, 32),
 ])
 def test_lattice_generator_and_sell_bit_exact(spec):
     kind, Lx, Ly, Lz, W, seed, C, sigma = spec
-    H = pkg.chebfd_matrix_create_lattice(kind, Lx, Ly, Lz, t=1.0, m=1.0, W=W, seed=seed,
+    m = 2.0 if kind == "topi_slab" else 1.0
+    H = pkg.chebfd_matrix_create_lattice(kind, Lx, Ly, Lz, t=1.0, m=m, W=W, seed=seed,
                                          sell_C=C, sell_sigma=sigma)
-    ref = osell.sell_from_csr(*oracle_csr(kind, Lx, Ly, Lz, 1.0, 1.0, W, seed), C, sigma)
+    ref = osell.sell_from_csr(*oracle_csr(kind, Lx, Ly, Lz, 1.0, m, W, seed), C, sigma)
     assert_sell_equal(H.export_sell(), ref)
 
 

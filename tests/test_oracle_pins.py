@@ -200,6 +200,28 @@ def test_graphene_structure_and_clean_spectrum():
     assert d.min() >= -0.5 and d.max() < 0.5
 
 
+def test_topi_slab_structure_and_clean_spectrum():
+    """Eq. Ham on a slab: the clean spectrum equals the union over (k_x, k_y)
+    of the layered chain built from the Bloch form (independent of the
+    real-space generator); surface rows have 11 entries, bulk rows 13; the
+    disorder sits on Gamma0 = 1, so tr H = 4 sum_s V_s (Gamma1 is traceless)."""
+    for L in ((4, 3, 5), (3, 4, 2), (5, 5, 1)):
+        rp, c, v = lattice.topi_slab_csr(*L, W=0.0)
+        H = lattice.to_scipy(rp, c, v)
+        assert (H - H.conj().T).count_nonzero() == 0
+        e = np.linalg.eigvalsh(H.toarray())
+        assert np.abs(e - lattice.topi_slab_clean_spectrum(*L)).max() < 1e-12
+    rp, c, v = lattice.topi_slab_csr(4, 3, 5, W=0.0)
+    lens = np.diff(rp).reshape(5, 3 * 4 * 4)           # rows grouped by layer z
+    assert np.all(lens[0] == 11) and np.all(lens[-1] == 11) and np.all(lens[1:-1] == 13)
+    rp, c, v = lattice.topi_slab_csr(4, 4, 6, m=2.0, W=2.0, seed=3)
+    H = lattice.to_scipy(rp, c, v)
+    V = lattice.disorder(3, 4 * 4 * 6, 2.0)
+    assert abs(H.diagonal().sum() - 4 * V.sum()) < 1e-11
+    d = H.diagonal().real.reshape(-1, 4)
+    assert np.array_equal(d[:, 0], V + 2.0) and np.array_equal(d[:, 3], V - 2.0)
+
+
 # ---------------------------------------------------------------- SELL
 
 
