@@ -340,7 +340,10 @@ chebfd_status chebfd_convert_block(const void* X, chebfd_dtype xdt, int64_t ldx,
  * ensemble stores its own copy (SELL chunk height sell_C), so the members
  * may be destroyed afterwards.  Rows of member i are [off_i, off_{i+1}) of
  * the ensemble; a search block for the ensemble is one row-major
- * N_total x nb device block.  Synchronizes. */
+ * N_total x nb device block.  When every member has a blocked copy (see
+ * chebfd_matrix_set_blocked) the ensemble concatenates them and its complex64
+ * Chebyshev steps run the blocked kernel, bit-identical per member to the
+ * member's own filter.  Synchronizes. */
 typedef struct chebfd_ensemble chebfd_ensemble;
 
 chebfd_status chebfd_ensemble_create(const chebfd_matrix* const* Hs, int count, int sell_C,

@@ -144,7 +144,8 @@ struct StepArgs {
     int mom_step;        // n of the step: writes mu_{2n-2}, mu_{2n-1} (SPMV: mu_0, mu_1)
     int tile;            // consecutive row groups per block and wave (0 = 1)
     // Ensemble of independent matrices (block-diagonal): per-instance
-    // coefficients coef[inst * coef_ld + {0: alpha, 1: beta, 2 + n: gc_n}],
+    // coefficients coef[inst * coef_ld + {0: alpha, 1: beta, 2 + n: gc_n,
+    // coef_ld - 1: beta / alpha (diagonal shift of the blocked step)}],
     // instance of each (original) row in row_inst.  nullptr: single matrix.
     const double* coef;
     const int32_t* row_inst;

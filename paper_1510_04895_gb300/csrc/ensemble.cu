@@ -66,6 +66,12 @@ __global__ void ens_chunk_uniform(int64_t nchunks, int C, int L, int64_t* chunk_
     }
 }
 
+__global__ void ens_fill_bell_cols(const int32_t* in, int64_t count, int32_t shift, int32_t* out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = in[t] + shift;
+}
+
 __global__ void fill_int_kernel(int32_t* p, int64_t n, int32_t v) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x)
@@ -81,7 +87,7 @@ struct chebfd_ensemble {
     int count = 0;
     std::vector<int64_t> offsets;     // count + 1 row offsets
     int32_t* row_inst = nullptr;      // instance of each row
-    double* coef = nullptr;           // [count][Np + 3]
+    double* coef = nullptr;           // [count][Np + 4]: alpha, beta, gc_0..gc_Np, beta/alpha
     int Np = 0;
     int panel = 0, tile = 0;          // tuned launch shape (0 = defaults)
     void* work = nullptr;             // U and W work vectors
@@ -101,6 +107,8 @@ void free_ensemble(chebfd_ensemble* E) {
     cudaFree(E->m.col);
     cudaFree(E->m.val64);
     cudaFree(E->m.val32);
+    cudaFree(E->m.bell_col);
+    cudaFree(E->m.bell_val32);
     cudaFree(E->row_inst);
     cudaFree(E->coef);
     cudaFree(E->work);
@@ -169,6 +177,27 @@ void ensemble_build(chebfd_ensemble* E, const chebfd_matrix* const* Hs, int coun
                 L, off, C, M.col, (double*)M.val64, (float*)M.val32);
         fill_int_kernel<<<grid_for(Mi.n), 256, 0, s>>>(E->row_inst + off, Mi.n, i);
     }
+    // blocked copy: the members' blocked copies one after the other, block
+    // columns shifted by the member's first block row (offsets are multiples
+    // of 4: every member dimension is)
+    bool blocked = single && cplx;
+    for (int i = 0; i < count && blocked; ++i)
+        blocked = Hs[i]->m.bell_col != nullptr && Hs[i]->m.n % kBellB == 0;
+    if (blocked) {
+        const int64_t nbr = n / kBellB;
+        const size_t vb = (size_t)kBellLB * kBellB * kBellB * sizeof(float2);
+        CHEBFD_CHECK_CUDA(cudaMalloc(&M.bell_col, nbr * kBellLB * sizeof(int32_t)));
+        CHEBFD_CHECK_CUDA(cudaMalloc(&M.bell_val32, nbr * vb));
+        for (int i = 0; i < count; ++i) {
+            const Matrix& Mi = Hs[i]->m;
+            const int64_t b0 = E->offsets[i] / kBellB, nbi = Mi.n / kBellB;
+            ens_fill_bell_cols<<<grid_for(nbi * kBellLB), 256, 0, s>>>(
+                Mi.bell_col, nbi * kBellLB, (int32_t)b0, M.bell_col + b0 * kBellLB);
+            CHEBFD_CHECK_CUDA(cudaMemcpyAsync((char*)M.bell_val32 + b0 * vb, Mi.bell_val32,
+                                              nbi * vb, cudaMemcpyDeviceToDevice, s));
+        }
+        M.bell_enabled = true;
+    }
     CHEBFD_CHECK_CUDA(cudaGetLastError());
     CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
     E->count = count;
@@ -177,12 +206,13 @@ void ensemble_build(chebfd_ensemble* E, const chebfd_matrix* const* Hs, int coun
 void set_coeffs(chebfd_ensemble* E, const double* alpha, const double* beta, const double* gc,
                 int Np, cudaStream_t s) {
     CHEBFD_REQUIRE(alpha && beta && gc && Np >= 2, CHEBFD_EINVAL, "bad coefficient arguments");
-    const int ldc = Np + 3;
+    const int ldc = Np + 4;
     std::vector<double> h((size_t)E->count * ldc);
     for (int i = 0; i < E->count; ++i) {
         h[(size_t)i * ldc] = alpha[i];
         h[(size_t)i * ldc + 1] = beta[i];
         for (int n = 0; n <= Np; ++n) h[(size_t)i * ldc + 2 + n] = gc[(size_t)i * (Np + 1) + n];
+        h[(size_t)i * ldc + Np + 3] = beta[i] / alpha[i];  // diagonal shift of the blocked step
     }
     if (Np != E->Np) {
         for (auto& kv : E->graphs) cudaGraphExecDestroy(kv.second);
@@ -223,7 +253,7 @@ void queue_filter(chebfd_ensemble* E, void* X, int64_t ld, int nb, chebfd_dtype 
         a.tile = E->tile;
         a.coef = E->coef;
         a.row_inst = E->row_inst;
-        a.coef_ld = Np + 3;
+        a.coef_ld = Np + 4;
         a.gather = Xp;
         a.ldg = ld;
         a.w = U;

@@ -55,7 +55,9 @@ __device__ __forceinline__ void cp_async_wait_prev() {
 // loads, so only the u gathers hold registers across memory latency (this
 // took the kernel from 0.65 to 0.84 of the measured HBM bandwidth against
 // keeping the values in registers).
-template <int G>
+// ENS: an ensemble of such matrices (block-diagonal); each block row reads
+// its member's 2 alpha, g_n c_n and beta/alpha from the coefficient table.
+template <int G, bool ENS>
 __global__ void __launch_bounds__(BELL_THREADS, 2)
     bell_step_kernel(BellView H, StepArgs a, int wc, float shift) {
     constexpr int B = kBellB, LB = kBellLB, SLOTS = BELL_THREADS / G, NV = LB * 8;
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(BELL_THREADS, 2)
     float* __restrict__ y = reinterpret_cast<float*>(a.y);
     const int64_t ldg = 2 * a.ldg, ldw = 2 * a.ldw, ldy = 2 * a.ldy;
     const int64_t cofs = 4 * (int64_t)lane;
-    const float2 ta = dup((float)(2.0 * a.alpha)), cc = dup((float)a.c0);
+    float2 ta = dup((float)(2.0 * a.alpha)), cc = dup((float)a.c0);
 
     const int tile = a.tile > 0 ? a.tile : 1;
     const int64_t wave = (int64_t)gridDim.x * tile * SLOTS;
@@ -97,6 +99,14 @@ __global__ void __launch_bounds__(BELL_THREADS, 2)
         const int32_t bc_cur = bc_next;
         bc_next = (br_next < H.nbr && lane < LB) ? __ldcs(H.bcol + br_next * LB + lane) : 0;
         stage(br_next, (it + 1) & 1);
+        if constexpr (ENS) {
+            if (active) {
+                const double* cf = a.coef + (int64_t)__ldg(a.row_inst + br * B) * a.coef_ld;
+                ta = dup(2.0f * (float)__ldg(cf));  // == (float)(2 alpha): doubling is exact
+                cc = dup((float)__ldg(cf + 2 + a.mom_step));
+                shift = (float)__ldg(cf + a.coef_ld - 1);
+            }
+        }
         if (active && on) {
 #pragma unroll
             for (int r = 0; r < B; ++r) {
@@ -171,12 +181,12 @@ __global__ void __launch_bounds__(BELL_THREADS, 2)
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-template <int G>
+template <int G, bool ENS>
 void launch_g(const BellView& v, const StepArgs& a, int wc, float shift, int sms,
               cudaStream_t s) {
     constexpr int SLOTS = BELL_THREADS / G;
     const size_t smem = (size_t)2 * SLOTS * kBellLB * 8 * sizeof(float4);
-    auto kern = bell_step_kernel<G>;
+    auto kern = bell_step_kernel<G, ENS>;
     static bool attr = false;
     if (!attr) {
         CHEBFD_CHECK_CUDA(
@@ -193,7 +203,8 @@ void launch_g(const BellView& v, const StepArgs& a, int wc, float shift, int sms
 bool bell_step_applies(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs& a,
                        int wc) {
     return M.bell_enabled && M.bell_col != nullptr && dt == CHEBFD_C64 && mode == MODE_STEP &&
-           a.moments == nullptr && a.coef == nullptr && wc >= 1 && wc <= 32;
+           a.moments == nullptr && (a.coef == nullptr || a.row_inst != nullptr) && wc >= 1 &&
+           wc <= 32;
 }
 
 void launch_bell_step(const Matrix& M, const StepArgs& a, int wc, cudaStream_t s) {
@@ -202,18 +213,22 @@ void launch_bell_step(const Matrix& M, const StepArgs& a, int wc, cudaStream_t s
         const char* e = getenv("CHEBFD_BELL_TILE");
         return e ? std::max(1, atoi(e)) : 1;
     }();
-    b.tile = env_tile;
+    b.tile = a.tile > 0 ? a.tile : env_tile;
     BellView v;
     v.bcol = M.bell_col;
     v.bval = reinterpret_cast<const float4*>(M.bell_val32);
     v.nbr = M.n / kBellB;
-    const float shift = (float)(a.beta / a.alpha);
+    const float shift = a.coef ? 0.f : (float)(a.beta / a.alpha);  // ensembles: per member
+    const bool ens = a.coef != nullptr;
     if (wc > 16)
-        launch_g<32>(v, b, wc, shift, M.num_sms, s);
+        ens ? launch_g<32, true>(v, b, wc, shift, M.num_sms, s)
+            : launch_g<32, false>(v, b, wc, shift, M.num_sms, s);
     else if (wc > 8)
-        launch_g<16>(v, b, wc, shift, M.num_sms, s);
+        ens ? launch_g<16, true>(v, b, wc, shift, M.num_sms, s)
+            : launch_g<16, false>(v, b, wc, shift, M.num_sms, s);
     else
-        launch_g<8>(v, b, wc, shift, M.num_sms, s);
+        ens ? launch_g<8, true>(v, b, wc, shift, M.num_sms, s)
+            : launch_g<8, false>(v, b, wc, shift, M.num_sms, s);
 }
 
 }  // namespace chebfd
