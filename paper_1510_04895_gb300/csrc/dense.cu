@@ -23,6 +23,11 @@ namespace chebfd {
 
 void spmv_impl(const Matrix& M, double alpha, double beta, const void* X, void* Y, int64_t ld,
                int nb, chebfd_dtype dt, cudaStream_t s);
+size_t df_gram_work_bytes(int m, int sms);
+void df_gram(bool cplx, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n,
+             int m, double* C, void* work, int sms, cudaStream_t s);
+void df_gemm(bool cplx, int r, int64_t n, int k, const double* Mt, int ldm, const double* Y,
+             int64_t ldy, double* T, int64_t ldt, cudaStream_t s);
 
 namespace {
 
@@ -481,8 +486,10 @@ void gemm_small(Handles& h, bool cplx, bool ah, int ns, const double* A, const d
 // (Y^H Y, Y1^H Y1, Y1^H H Y1) and three block GEMMs (Y T1, V, HV) instead of
 // the five + three of the separate calls.  A rank drop in the second pass
 // falls back to the separate calls.  Y <- Ritz vectors (ascending theta).
+// df: the six tall products in double-float arithmetic (df_dense.cu) instead
+// of cuBLAS FP64; the n_s x n_s steps stay FP64.
 void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype dt, uint64_t seed,
-                   int64_t* refill_counter, double* theta_host, double* res_host,
+                   int64_t* refill_counter, double* theta_host, double* res_host, bool df,
                    cudaStream_t s) {
     check_fp64_block(dt, Yv, M.n, ns, ld);
     const bool cplx = dt == CHEBFD_C128;
@@ -496,6 +503,20 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
         T((size_t)n * ld * es, s);
     std::vector<double> hth(ns);
     int64_t counter = refill_counter ? *refill_counter : 0;
+    // tall products: cuBLAS FP64, or double-float kernels (df)
+    Buf dfwork(df ? df_gram_work_bytes(ns, M.num_sms) : 0, s);
+    auto tall_gram = [&](const double* A, const double* B, double* C) {
+        if (df)
+            df_gram(cplx, A, ld, B, ld, n, ns, C, dfwork.p, M.num_sms, s);
+        else
+            gemm_nh(h, cplx, ns, n, A, ld, B, ld, C, ns);
+    };
+    auto tall_gemm = [&](int r, const double* Mc, const double* Yb, double* Tb) {
+        if (df)
+            df_gemm(cplx, r, n, ns, Mc, ns, Yb, ld, Tb, ld, s);
+        else
+            gemm_ch(h, cplx, r, n, ns, Mc, ns, Yb, ld, Tb, ld);
+    };
 
     // SVQB pass on the block B (already Gram'ed into S): scale, eigensolve,
     // transform columns; returns the rank kept.
@@ -523,9 +544,9 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
     };
 
     // ---- pass 1: Y1 = Y T1 (+ refill) into T
-    gram(h, cplx, Y, n, ns, ld, S.as<double>());
+    tall_gram(Y, Y, S.as<double>());
     const int r1 = svqb_transform();
-    gemm_ch(h, cplx, r1, n, ns, Mt.as<double>(), ns, Y, ld, T.as<double>(), ld);
+    tall_gemm(r1, Mt.as<double>(), Y, T.as<double>());
     if (r1 < ns) {
         if (cplx)
             refill_kernel<true><<<grid1d(n * (ns - r1)), 256, 0, s>>>(T.as<double>(), n, ld, r1,
@@ -536,7 +557,7 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
         counter += ns - r1;
     }
     // ---- pass 2: T2 from Y1^H Y1, kept in Mt (stored conj(T2))
-    gram(h, cplx, T.as<double>(), n, ns, ld, S.as<double>());
+    tall_gram(T.as<double>(), T.as<double>(), S.as<double>());
     const int r2 = svqb_transform();
     if (r2 < ns) {
         // rank drop after pass 1: the separate, up to three-pass path
@@ -551,7 +572,7 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
     Buf HY((size_t)n * ld * es, s), G((size_t)ns * ns * es, s), W2((size_t)ns * ns * es, s),
         res((size_t)ns * sizeof(double), s);
     spmv_impl(M, 1.0, 0.0, T.p, HY.p, ld, ns, dt, s);
-    gemm_nh(h, cplx, ns, n, HY.as<double>(), ld, T.as<double>(), ld, G.as<double>(), ns);
+    tall_gram(HY.as<double>(), T.as<double>(), G.as<double>());
     // stored conj(A2) = Mt^H conj(A1) Mt with conj(A1) in G
     gemm_small(h, cplx, false, ns, G.as<double>(), Mt.as<double>(), W2.as<double>());
     gemm_small(h, cplx, true, ns, Mt.as<double>(), W2.as<double>(), G.as<double>());
@@ -562,8 +583,8 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
     heev(h, cplx, G.as<double>(), ns, th.as<double>(), s);
     // C = Mt E (stored conj of T2 S); V = Y1 conj(C), HV = HY1 conj(C)
     gemm_small(h, cplx, false, ns, Mt.as<double>(), G.as<double>(), W2.as<double>());
-    gemm_ch(h, cplx, ns, n, ns, W2.as<double>(), ns, T.as<double>(), ld, Y, ld);
-    gemm_ch(h, cplx, ns, n, ns, W2.as<double>(), ns, HY.as<double>(), ld, T.as<double>(), ld);
+    tall_gemm(ns, W2.as<double>(), T.as<double>(), Y);
+    tall_gemm(ns, W2.as<double>(), HY.as<double>(), T.as<double>());
     residuals_from_blocks(cplx, T.as<double>(), Y, th.as<double>(), n, ld, ns, res.as<double>(), s);
     CHEBFD_CHECK_CUDA(cudaMemcpyAsync(theta_host, th.p, ns * sizeof(double),
                                       cudaMemcpyDeviceToHost, s));

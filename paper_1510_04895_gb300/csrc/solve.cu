@@ -12,7 +12,7 @@ namespace chebfd {
 void filter_block_df_impl(const Matrix& M, double alpha, double beta, const double* gc, int Np,
                           void* X, int64_t ld, int nb, cudaStream_t s);
 void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype dt, uint64_t seed,
-                   int64_t* refill_counter, double* theta_host, double* res_host,
+                   int64_t* refill_counter, double* theta_host, double* res_host, bool df,
                    cudaStream_t s);
 
 void filter_block_impl(const Matrix& M, double alpha, double beta, const double* gc, int Np,
@@ -144,7 +144,7 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
         double t1 = now();
         t_filter += t1 - t0;
         // ---- steps 6-7: orthonormalise, Rayleigh-Ritz
-        ortho_rr_impl(M, Y64.p, ld, ns, d64, p.seed, &refill, theta.data(), res.data(), s);
+        ortho_rr_impl(M, Y64.p, ld, ns, d64, p.seed, &refill, theta.data(), res.data(), df, s);
         t_dense += now() - t1;
         // ---- step 8: window membership, ghosts, convergence
         acc_idx.clear();
