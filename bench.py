@@ -496,12 +496,16 @@ def run_ours(args):
 
     if not args.no_ensemble and w["kind"] == "topi":
         out["ensemble"] = bench_ensemble(pkg, workloads, dev, peaks["hbm_gbs"])
+    torch.cuda.empty_cache()     # the solve allocates its own blocks
     if not args.no_solve:
         # the MLP was trained on insulators only: learned parameters for those
-        out["time_to_solution"] = bench_solve(pkg, H, a, b, delta, Np, ns, w["label"],
-                                              learned=w["kind"] == "topi",
-                                              chiral=w["kind"] == "topi",
-                                              precisions=args.solve_precisions)
+        try:
+            out["time_to_solution"] = bench_solve(pkg, H, a, b, delta, Np, ns, w["label"],
+                                                  learned=w["kind"] == "topi",
+                                                  chiral=w["kind"] == "topi",
+                                                  precisions=args.solve_precisions)
+        except pkg.ChebFDError as e:     # reported, the throughput line still prints
+            out["time_to_solution"] = {"error": str(e)}
 
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, desc = oracle_sample(w, a, b, delta, args.cpu_steps)

@@ -69,21 +69,27 @@ def disorder(seed, count, W):
     return W * (u - 0.5)
 
 
-def topi_csr(Lx, Ly, Lz, t=1.0, m=1.0, W=0.0, seed=0):
-    """CSR (rowptr int64, col int32, val complex128) of the insulator Hamiltonian."""
-    nsite = Lx * Ly * Lz
+def topi_csr(Lx, Ly, Lz, t=1.0, m=1.0, W=0.0, seed=0, sites=None):
+    """CSR (rowptr int64, col int32, val complex128) of the insulator Hamiltonian.
+    With `sites` (an int64 array of site indices) only the 4 rows of each
+    listed site are generated: the CSR then has 4 len(sites) rows, row 4 q + o
+    being row 4 sites[q] + o of the full matrix (columns stay global)."""
+    nsite_all = Lx * Ly * Lz
+    s = np.arange(nsite_all, dtype=np.int64) if sites is None else np.asarray(sites, np.int64)
+    nsite = len(s)
     n = 4 * nsite
-    s = np.arange(nsite, dtype=np.int64)
     x = s % Lx
     y = (s // Lx) % Ly
     z = s // (Lx * Ly)
-    V = disorder(seed, nsite, W)
+    V = disorder(seed, nsite_all, W)[s] if sites is None else W * (
+        rng.uniform(seed, rng.STREAM_DISORDER, s.astype(np.uint64)) - 0.5)
     mv = m + V                                   # one rounding per site
     h = t / 2.0
     rows, cols, vals, order = [], [], [], []
     g1 = np.real(np.diag(GAMMA[0]))              # +1, +1, -1, -1
+    q_local = np.arange(nsite, dtype=np.int64)
     for o in range(4):
-        r = 4 * s + o
+        r = 4 * q_local + o                      # local row (= global row for the full matrix)
         # onsite (m + V_s) Gamma1
         rows.append(r); cols.append(4 * s + o)
         vals.append((mv if g1[o] > 0 else -mv).astype(np.complex128))

@@ -320,9 +320,11 @@ __global__ void bell_fill_kernel(const int64_t* rowptr, const int32_t* ccol, con
         }
         for (int k = 0; k < kBellLB; ++k) {
             bcol[br * kBellLB + k] = cols[k];
-            for (int e = 0; e < kBellB * kBellB; ++e)
-                bval[(br * kBellLB + k) * (kBellB * kBellB) + e] =
-                    make_float2(__double2float_rn(acc[k][e].x), __double2float_rn(acc[k][e].y));
+            for (int e = 0; e < kBellB * kBellB; ++e) {
+                const int64_t q = (br * kBellLB + k) * (kBellB * kBellB) + e;
+                bval[q] = make_float2(__double2float_rn(acc[k][e].x),
+                                      __double2float_rn(acc[k][e].y));
+            }
         }
     }
 }

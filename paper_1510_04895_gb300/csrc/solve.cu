@@ -200,6 +200,16 @@ void fill_result(chebfd_result* R, const std::vector<int>& acc, const std::vecto
                  size_t es, int iterations, bool converged, int fp64_its, int64_t n_mvm,
                  double a, double b, cudaStream_t s) {
     const int nev = (int)acc.size();
+    // the stream-ordered pool keeps the iteration's freed blocks; hand them
+    // back before the result's own allocation
+    {
+        int dev = 0;
+        cudaMemPool_t pool;
+        CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+            cudaMemPoolTrimTo(pool, 0);
+    }
     R->lambda.resize(nev);
     R->res.resize(nev);
     R->n = n;

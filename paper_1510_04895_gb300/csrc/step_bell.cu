@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include "async_copy.cuh"
 #include "filter_kernels.cuh"
 
 namespace chebfd {
@@ -28,22 +29,7 @@ struct BellView {
     int64_t nbr;
 };
 
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 __device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_prev() {
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-}
 
 // G lanes per block row; lane < wc owns one 16-byte chunk (two complex
 // columns) of the 4 rows.  Block rows are visited in the same wave-front
@@ -178,7 +164,7 @@ __global__ void __launch_bounds__(BELL_THREADS, 2)
         br = br_next;
         tt = tt + 1 == tile ? 0 : tt + 1;
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    cp_async_wait_all();
 }
 
 template <int G, bool ENS>

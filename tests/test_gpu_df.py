@@ -102,3 +102,16 @@ def test_df_filter_needs_the_single_copy():
     X = torch.zeros((H.n, 8), dtype=torch.complex128, device=DEV)
     with pytest.raises(pkg.ChebFDError):
         pkg.chebfd_filter_block_df(H, 0.2, 0.0, np.ones(5), X)
+
+
+@pytest.mark.parametrize("blocked", [True, False])
+def test_df_filter_slab_blocked_and_sell(blocked):
+    """Eq. Ham slab: the blocked double-float step (site blocks, padded at
+    the open surfaces) and the SELL one both within 1e-11 of the oracle."""
+    H = pkg.chebfd_matrix_create_lattice("topi_slab", 5, 6, 4, t=1.0, m=2.0, W=2.0, seed=2,
+                                         also_single=True)
+    assert H.blocked_width == 7
+    H.set_blocked(blocked)
+    Ho = lattice.to_scipy(*lattice.topi_slab_csr(5, 6, 4, t=1.0, m=2.0, W=2.0, seed=2))
+    got, ref = _df_case(H, Ho, 40, 90, "lanczos", (-0.06, 0.06))
+    assert rel(got, ref) <= 1e-11, rel(got, ref)

@@ -200,6 +200,20 @@ def test_graphene_structure_and_clean_spectrum():
     assert d.min() >= -0.5 and d.max() < 0.5
 
 
+def test_topi_rows_of_selected_sites_equal_full_matrix_rows():
+    """The site-restricted generator (used for sampled checks at N = 16e6)
+    gives exactly the rows of the full matrix."""
+    full = lattice.to_scipy(*lattice.topi_csr(5, 4, 6, W=1.3, seed=7)).toarray()
+    sites = np.array([0, 7, 33, 119])
+    rp, c, v = lattice.topi_csr(5, 4, 6, W=1.3, seed=7, sites=sites)
+    rows = (4 * sites[:, None] + np.arange(4)).ravel()
+    dense = np.zeros((len(rows), full.shape[1]), complex)
+    for i in range(len(rows)):
+        for p in range(rp[i], rp[i + 1]):
+            dense[i, c[p]] += v[p]
+    assert np.array_equal(dense, full[rows])
+
+
 def test_topi_slab_structure_and_clean_spectrum():
     """Eq. Ham on a slab: the clean spectrum equals the union over (k_x, k_y)
     of the layered chain built from the Bloch form (independent of the
