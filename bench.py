@@ -457,6 +457,17 @@ def run_ours(args):
             dtype_name, nb), "launch_us": t_sell * 1e6,
             "achieved": bytes_launch / t_sell / 1e9,
             "frac": bytes_launch / t_sell / 1e9 / peaks["hbm_gbs"]}
+    if single and w["kind"] == "topi":
+        # matrix-free step: the insulator's entries rebuilt in registers
+        H.set_matrix_free(True)
+        t_mf = time_step()
+        H.set_matrix_free(False)
+        roof["matrix_free_kernel"] = {
+            "kernel": "stencil_step_kernel (MODE_STEP, %s, n_b=%d)" % (dtype_name, nb),
+            "launch_us": t_mf * 1e6, "achieved": bytes_launch / t_mf / 1e9,
+            "frac": bytes_launch / t_mf / 1e9 / peaks["hbm_gbs"],
+            "vector_bytes_per_launch": N * 5 * nb * S_v,
+            "vector_gbs": N * 5 * nb * S_v / t_mf / 1e9}
     del U, Wv, Y
 
     # ---- end to end through the C ABI with host buffers ------------------------

@@ -59,6 +59,7 @@ SIGNATURES = {
     "chebfd_matrix_export_sell": (ctypes.c_int, [c_vp, c_i64p, c_i32p, c_i32p, c_vp, c_i64p]),
     "chebfd_matrix_destroy": (ctypes.c_int, [c_vp]),
     "chebfd_matrix_set_blocked": (ctypes.c_int, [c_vp, ctypes.c_int]),
+    "chebfd_matrix_set_matrix_free": (ctypes.c_int, [c_vp, ctypes.c_int]),
     "chebfd_spmv": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double, c_vp, c_vp,
                                    ctypes.c_int64, ctypes.c_int, ctypes.c_int, c_vp]),
     "chebfd_scale_bounds": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_uint64, c_dp, c_dp, c_dp,
@@ -230,6 +231,11 @@ class Matrix:
         """Use (True) or bypass (False) the blocked copy in the complex64 step."""
         _check(lib().chebfd_matrix_set_blocked(self.handle, 1 if enable else 0),
                "chebfd_matrix_set_blocked")
+
+    def set_matrix_free(self, enable):
+        """Rebuild the insulator's entries in registers in the complex64 step."""
+        _check(lib().chebfd_matrix_set_matrix_free(self.handle, 1 if enable else 0),
+               "chebfd_matrix_set_matrix_free")
 
     def close(self):
         if self.handle:

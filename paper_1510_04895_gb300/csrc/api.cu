@@ -466,6 +466,8 @@ chebfd_status chebfd_matrix_create_lattice(const chebfd_lattice_desc* desc, void
             M.complex_values = desc->kind != CHEBFD_LATTICE_GRAPHENE;
             build_sell_from_device_csr(M, d_rowptr, d_col, d_val, desc->sell_C,
                                        desc->sell_sigma, desc->also_single != 0, s);
+            M.gen = *desc;
+            M.has_gen = true;
         } catch (...) {
             cudaFree(d_rowptr);
             cudaFree(d_col);
@@ -496,6 +498,20 @@ chebfd_status chebfd_matrix_get_info(const chebfd_matrix* H, chebfd_matrix_info*
         out->is_complex = M.complex_values ? 1 : 0;
         out->has_single = M.val32 ? 1 : 0;
         out->blocked_width = M.bell_col ? kBellLB : 0;
+    });
+}
+
+chebfd_status chebfd_matrix_set_matrix_free(chebfd_matrix* H, int enable) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(H, CHEBFD_EINVAL, "null matrix");
+        const Matrix& M = H->m;
+        const bool ok = M.has_gen && M.val32 != nullptr && M.identity_perm &&
+                        (M.gen.kind == CHEBFD_LATTICE_TOPI ||
+                         M.gen.kind == CHEBFD_LATTICE_TOPI_SLAB);
+        CHEBFD_REQUIRE(!enable || ok, CHEBFD_EUNSUPPORTED,
+                       "matrix-free step needs an insulator lattice built with also_single and "
+                       "sell_sigma = 1");
+        H->m.stencil_enabled = enable != 0;
     });
 }
 

@@ -98,6 +98,11 @@ struct Matrix {
     int32_t* bell_col = nullptr;
     void* bell_val32 = nullptr;
     bool bell_enabled = false;
+    // Generator of a lattice matrix (has_gen), for the matrix-free insulator
+    // step that rebuilds the entries in registers (stencil_enabled).
+    chebfd_lattice_desc gen{};
+    bool has_gen = false;
+    bool stencil_enabled = false;
     // Row panel order used by the kernels (same as sorted order here).
     int device = 0;
     int num_sms = 0;
@@ -127,6 +132,28 @@ void generate_lattice_csr(const chebfd_lattice_desc& d, int64_t* n_out, int64_t*
 
 enum StepMode { MODE_SPMV = 0, MODE_SECOND = 1, MODE_STEP = 2 };
 
+// Visiting order of the sites of an Lx x Ly x Lz lattice (4 rows per site)
+// for the step kernels: tiles of TX x TY sites of the x-y plane, all z of a
+// tile before the next tile, so that the z-neighbours of a tile are gathered
+// while still in L2 (a whole 200 x 200 plane of a 64-column complex64 block
+// is 82 MB).  Visit index q -> site.  TX | Lx and TY | Ly; enabled == 0: q is
+// the site itself.
+struct SiteOrder {
+    int enabled;
+    int Lx, Ly, Lz, TX, TY;
+    __device__ __forceinline__ int64_t site(int64_t q) const {
+        if (!enabled) return q;
+        const int qi = (int)q;  // < 2^29 sites
+        const int plane = TX * TY, per_tile = plane * Lz;
+        const int tile = qi / per_tile, rem = qi - tile * per_tile;
+        const int z = rem / plane, l = rem - z * plane;
+        const int ly = l / TX, lx = l - ly * TX;
+        const int ntx = Lx / TX;
+        const int ty = tile / ntx, tx = tile - ty * ntx;
+        return (int64_t)(tx * TX + lx) + (int64_t)Lx * ((ty * TY + ly) + (int64_t)Ly * z);
+    }
+};
+
 struct StepArgs {
     // Vectors (row-major, ld elements per row).
     const void* gather;  // u: gathered through H (input of the product)
@@ -150,7 +177,12 @@ struct StepArgs {
     const double* coef;
     const int32_t* row_inst;
     int coef_ld;
+    SiteOrder order;     // site visiting order of lattice matrices (set by launch_step)
 };
+
+// The site order for a generated insulator lattice and a panel of wc
+// 16-byte chunks per row (tiled when two planes of u rows exceed L2).
+SiteOrder site_order_of(const Matrix& M, int wc);
 
 // Launch one step kernel.  dt selects the vector type, `single` the matrix copy.
 void launch_step(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs& a,

@@ -1,0 +1,214 @@
+// Matrix-free complex64 Chebyshev step (MODE_STEP) for the insulator
+// lattices: w = 2 (alpha H + beta) u - w ; y += c w with H's entries rebuilt
+// in registers from the lattice description instead of read from memory
+// (the paper's on-the-fly matrices, Sec. 1).
+//
+// Same mapping as the blocked step (step_bell.cu): one group of G lanes per
+// site computes its 4 orbital rows, each lane one 16-byte chunk (two complex
+// columns), gathering each neighbour site's 4 rows once.  The entries follow
+// the generator: onsite (m + V_s) Gamma1 (TOPI) or V_s + m Gamma1 (TOPI_SLAB)
+// with V_s regenerated from the SplitMix64 disorder stream, and for each
+// axis j the hopping block T_j = -(t/2)(Gamma1 - i Gamma_{j+1}) at the site
+// below and T_j^dagger at the site above: row o couples to orbital o with
+// -(t/2) Gamma1[o][o] and to its Gamma_{j+1} partner p with a purely real or
+// purely imaginary value.  Only the vectors move: 5 n_b S_v bytes per row.
+#include <algorithm>
+#include <cstdlib>
+
+#include "async_copy.cuh"
+#include "filter_kernels.cuh"
+
+namespace chebfd {
+
+namespace {
+
+constexpr int ST_THREADS = 256;
+
+struct StencilView {
+    int64_t Lx, Ly, Lz, nsite;
+    float h;        // t / 2
+    double m, W;
+    uint64_t seed;
+    int slab;       // open in z
+};
+
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
+// acc += a u (real a) and acc += i b u (imaginary b) on a 16-byte chunk of two
+// complex entries held as two float2 (re, im).
+__device__ __forceinline__ void mac_re(float2* acc, float a, const float4& u) {
+    acc[0] = __ffma2_rn(dup2(a), make_float2(u.x, u.y), acc[0]);
+    acc[1] = __ffma2_rn(dup2(a), make_float2(u.z, u.w), acc[1]);
+}
+__device__ __forceinline__ void mac_im(float2* acc, float b, const float4& u) {
+    const float2 bb = make_float2(-b, b);
+    acc[0] = __ffma2_rn(bb, make_float2(u.y, u.x), acc[0]);
+    acc[1] = __ffma2_rn(bb, make_float2(u.w, u.z), acc[1]);
+}
+
+// Add the hopping block of axis j (0, 1, 2) from a neighbour site whose 4
+// rows are g: q = +1 for the site below (T_j), -1 for the site above (T_j^dagger).
+template <int J>
+__device__ __forceinline__ void hop(float2 (*acc)[2], const float4* g, float h, float q) {
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        const bool upper = o < 2;
+        mac_re(acc[o], upper ? -h : h, g[o]);  // -h Gamma1[o][o]
+        // partner p and Gamma_{j+1}[o][p] = gr + i gi; entry q i h (gr + i gi)
+        if (J == 0) {        // sx (x) sx: real 1
+            mac_im(acc[o], q * h, g[o ^ 3]);
+        } else if (J == 1) { // sx (x) sy: -i for o = 0, 2; +i for o = 1, 3
+            const float gi = (o == 0 || o == 2) ? -1.f : 1.f;
+            mac_re(acc[o], -q * h * gi, g[o ^ 3]);
+        } else {             // sx (x) sz: +1 for o = 0, 2; -1 for o = 1, 3
+            const float gr = (o == 0 || o == 2) ? 1.f : -1.f;
+            mac_im(acc[o], q * h * gr, g[o ^ 2]);
+        }
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(ST_THREADS, 3)
+    stencil_step_kernel(StencilView L, StepArgs a, int wc, float shift) {
+    constexpr int B = 4, SLOTS = ST_THREADS / G;
+    const int lane = threadIdx.x % G, slot = threadIdx.x / G;
+    const bool on = lane < wc;
+    const float* __restrict__ u = reinterpret_cast<const float*>(a.gather);
+    float* __restrict__ w = reinterpret_cast<float*>(a.w);
+    float* __restrict__ y = reinterpret_cast<float*>(a.y);
+    const int64_t ldg = 2 * a.ldg, ldw = 2 * a.ldw, ldy = 2 * a.ldy;  // floats per row
+    const int64_t cofs = 4 * (int64_t)lane;
+    const float2 ta = dup2((float)(2.0 * a.alpha)), cc = dup2((float)a.c0);
+
+    const int tile = a.tile > 0 ? a.tile : 1;
+    const int64_t wave = (int64_t)gridDim.x * tile * SLOTS;
+    const int iters = (int)((L.nsite + wave - 1) / wave) * tile;
+    const int64_t wrap = wave - (int64_t)(tile - 1) * SLOTS;
+    int64_t q = (int64_t)blockIdx.x * tile * SLOTS + slot;  // visit index; site = order.site(q)
+    int tt = 0;
+
+    for (int it = 0; it < iters; ++it) {
+        const int64_t q_next = tt + 1 == tile ? q + wrap : q + SLOTS;
+        if (q < L.nsite && on) {
+            const int64_t s = a.order.site(q);
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                prefetch_l2(w + (s * B + r) * ldw + cofs);
+                prefetch_l2(y + (s * B + r) * ldy + cofs);
+            }
+            const int si = (int)s, Lx = (int)L.Lx, Ly = (int)L.Ly;  // sites < 2^29
+            const int64_t x = si % Lx, yy = (si / Lx) % Ly, z = si / (Lx * Ly);
+            auto site = [&](int64_t cx, int64_t cy, int64_t cz) {
+                return cx + L.Lx * (cy + L.Ly * cz);
+            };
+            auto gather = [&](int64_t sn, float4* g) {
+                const float* base = u + sn * B * ldg + cofs;
+#pragma unroll
+                for (int o = 0; o < B; ++o)
+                    g[o] = __ldg(reinterpret_cast<const float4*>(base + o * ldg));
+            };
+            float2 acc[B][2];
+#pragma unroll
+            for (int r = 0; r < B; ++r) acc[r][0] = acc[r][1] = make_float2(0.f, 0.f);
+            float4 g[B];
+            // onsite, with the shift beta/alpha
+            gather(s, g);
+            // the generator's roundings: V = W (u - 1/2), then m + V or V +- m
+            const double V =
+                __dmul_rn(L.W, splitmix_uniform(L.seed, STREAM_DISORDER, (uint64_t)s) - 0.5);
+            float on_up, on_lo;
+            if (L.slab) {
+                on_up = __double2float_rn(__dadd_rn(V, L.m));
+                on_lo = __double2float_rn(__dadd_rn(V, -L.m));
+            } else {
+                on_up = __double2float_rn(__dadd_rn(L.m, V));
+                on_lo = -on_up;
+            }
+#pragma unroll
+            for (int o = 0; o < B; ++o) mac_re(acc[o], (o < 2 ? on_up : on_lo) + shift, g[o]);
+            // x neighbours (periodic)
+            gather(site((x + L.Lx - 1) % L.Lx, yy, z), g);
+            hop<0>(acc, g, L.h, 1.f);
+            gather(site((x + 1) % L.Lx, yy, z), g);
+            hop<0>(acc, g, L.h, -1.f);
+            // y neighbours (periodic)
+            gather(site(x, (yy + L.Ly - 1) % L.Ly, z), g);
+            hop<1>(acc, g, L.h, 1.f);
+            gather(site(x, (yy + 1) % L.Ly, z), g);
+            hop<1>(acc, g, L.h, -1.f);
+            // z neighbours (periodic, or open for the slab)
+            if (!L.slab || z > 0) {
+                gather(site(x, yy, (z + L.Lz - 1) % L.Lz), g);
+                hop<2>(acc, g, L.h, 1.f);
+            }
+            if (!L.slab || z + 1 < L.Lz) {
+                gather(site(x, yy, (z + 1) % L.Lz), g);
+                hop<2>(acc, g, L.h, -1.f);
+            }
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                const int64_t row = s * B + r;
+                const float4 wo = __ldcs(reinterpret_cast<const float4*>(w + row * ldw + cofs));
+                const float4 yo = __ldcs(reinterpret_cast<const float4*>(y + row * ldy + cofs));
+                const float2 w0 = __ffma2_rn(ta, acc[r][0], make_float2(-wo.x, -wo.y));
+                const float2 w1 = __ffma2_rn(ta, acc[r][1], make_float2(-wo.z, -wo.w));
+                const float2 y0 = __ffma2_rn(cc, w0, make_float2(yo.x, yo.y));
+                const float2 y1 = __ffma2_rn(cc, w1, make_float2(yo.z, yo.w));
+                __stcs(reinterpret_cast<float4*>(w + row * ldw + cofs),
+                       make_float4(w0.x, w0.y, w1.x, w1.y));
+                __stcs(reinterpret_cast<float4*>(y + row * ldy + cofs),
+                       make_float4(y0.x, y0.y, y1.x, y1.y));
+            }
+        }
+        q = q_next;
+        tt = tt + 1 == tile ? 0 : tt + 1;
+    }
+}
+
+template <int G>
+void launch_g(const StencilView& v, const StepArgs& a, int wc, float shift, int sms,
+              cudaStream_t s) {
+    auto kern = stencil_step_kernel<G>;
+    const int grid =
+        sms * std::min(8, cached_occupancy(reinterpret_cast<const void*>(kern), ST_THREADS, 0));
+    kern<<<grid, ST_THREADS, 0, s>>>(v, a, wc, shift);
+}
+
+}  // namespace
+
+bool stencil_step_applies(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs& a,
+                          int wc) {
+    return M.stencil_enabled && M.has_gen && dt == CHEBFD_C64 && mode == MODE_STEP &&
+           a.moments == nullptr && a.coef == nullptr && wc >= 1 && wc <= 32;
+}
+
+void launch_stencil_step(const Matrix& M, const StepArgs& a, int wc, cudaStream_t s) {
+    StencilView v;
+    v.Lx = M.gen.Lx;
+    v.Ly = M.gen.Ly;
+    v.Lz = M.gen.Lz;
+    v.nsite = v.Lx * v.Ly * v.Lz;
+    v.h = (float)(M.gen.t / 2.0);
+    v.m = M.gen.m;
+    v.W = M.gen.W;
+    v.seed = M.gen.seed;
+    v.slab = M.gen.kind == CHEBFD_LATTICE_TOPI_SLAB ? 1 : 0;
+    StepArgs b = a;
+    static const int env_tile = [] {
+        const char* e = getenv("CHEBFD_BELL_TILE");
+        return e ? std::max(1, atoi(e)) : 1;
+    }();
+    b.tile = env_tile;
+    const float shift = (float)(a.beta / a.alpha);
+    if (wc > 16)
+        launch_g<32>(v, b, wc, shift, M.num_sms, s);
+    else if (wc > 8)
+        launch_g<16>(v, b, wc, shift, M.num_sms, s);
+    else if (wc > 4)
+        launch_g<8>(v, b, wc, shift, M.num_sms, s);
+    else
+        launch_g<4>(v, b, wc, shift, M.num_sms, s);
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+}
+
+}  // namespace chebfd

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(BELL_THREADS, 2)
     const int64_t wave = (int64_t)gridDim.x * tile * SLOTS;
     const int iters = (int)((H.nbr + wave - 1) / wave) * tile;
     const int64_t wrap = wave - (int64_t)(tile - 1) * SLOTS;
-    int64_t br = (int64_t)blockIdx.x * tile * SLOTS + slot;
+    int64_t q = (int64_t)blockIdx.x * tile * SLOTS + slot;  // visit index; site = order.site(q)
     int tt = 0;
 
     auto stage = [&](int64_t row, int buf) {
@@ -76,12 +76,15 @@ __global__ void __launch_bounds__(BELL_THREADS, 2)
         cp_async_commit();
     };
 
-    int32_t bc_next = (br < H.nbr && lane < LB) ? __ldcs(H.bcol + br * LB + lane) : 0;
-    stage(br, 0);
+    const int64_t s0 = q < H.nbr ? a.order.site(q) : H.nbr;
+    int32_t bc_next = (s0 < H.nbr && lane < LB) ? __ldcs(H.bcol + s0 * LB + lane) : 0;
+    stage(s0, 0);
 
     for (int it = 0; it < iters; ++it) {
-        const int64_t br_next = tt + 1 == tile ? br + wrap : br + SLOTS;
-        const bool active = br < H.nbr;
+        const int64_t q_next = tt + 1 == tile ? q + wrap : q + SLOTS;
+        const bool active = q < H.nbr;
+        const int64_t br = active ? a.order.site(q) : 0;
+        const int64_t br_next = q_next < H.nbr ? a.order.site(q_next) : H.nbr;
         const int32_t bc_cur = bc_next;
         bc_next = (br_next < H.nbr && lane < LB) ? __ldcs(H.bcol + br_next * LB + lane) : 0;
         stage(br_next, (it + 1) & 1);
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(BELL_THREADS, 2)
                        make_float4(y0.x, y0.y, y1.x, y1.y));
             }
         }
-        br = br_next;
+        q = q_next;
         tt = tt + 1 == tile ? 0 : tt + 1;
     }
     cp_async_wait_all();

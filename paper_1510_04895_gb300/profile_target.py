@@ -1,9 +1,10 @@
 """Profiling targets: small, self-contained launch sequences for ncu.
 
-    python -m paper_1510_04895_gb300.profile_target [topi|graphene] [n_b] [c64|c128|r32|r64] [sell]
+    python -m paper_1510_04895_gb300.profile_target [topi|graphene] [n_b] [c64|c128|r32|r64] [sell|free]
         five fused Chebyshev steps on one benchmark lattice (topi: the
         64x64x32x4 insulator, N = 524288; graphene: the 1024x1024 honeycomb
-        lattice, N = 2097152); `sell` bypasses the insulator's blocked copy.
+        lattice, N = 2097152); `sell` bypasses the insulator's blocked copy,
+        `free` runs the matrix-free step.
     python -m paper_1510_04895_gb300.profile_target df [n_b]
         one double-float filter of degree 8 on the insulator (n_b columns).
     python -m paper_1510_04895_gb300.profile_target solve [fp64|mixed_df]
@@ -43,6 +44,8 @@ else:
           "r64": torch.float64}[prec]
     if len(sys.argv) > 4 and sys.argv[4] == "sell" and H.blocked_width:
         H.set_blocked(False)            # row-wise SELL kernel instead of the blocked one
+    if len(sys.argv) > 4 and sys.argv[4] == "free":
+        H.set_matrix_free(True)         # entries rebuilt in registers
     U = torch.empty((H.n, nb), dtype=dt, device="cuda")
     W = torch.empty_like(U)
     Y = torch.zeros_like(U)

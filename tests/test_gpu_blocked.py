@@ -136,3 +136,69 @@ def test_slab_filter_matches_oracle(single):
     err = rel(X.cpu().numpy(), ref)
     tol = 120 * 30 * 2.0 ** -24 * np.linalg.norm(Xin) / np.linalg.norm(ref) if single else 1e-11
     assert err <= tol, (err, tol)
+
+
+@pytest.mark.parametrize("kind,L,nb", [("topi", (6, 5, 4), 64), ("topi", (5, 3, 7), 32),
+                                       ("topi", (2, 2, 3), 16), ("topi", (1, 3, 2), 8),
+                                       ("topi_slab", (6, 5, 4), 64), ("topi_slab", (3, 4, 2), 2),
+                                       ("topi_slab", (4, 4, 1), 16)])
+def test_matrix_free_step_matches_oracle(kind, L, nb):
+    """The matrix-free step (entries rebuilt in registers from the lattice
+    description; coinciding neighbours on edges 1 and 2; open slab surfaces)
+    within FP32 rounding of the FP64 oracle step and of the stored-matrix step."""
+    m = 2.0 if kind == "topi_slab" else 1.0
+    H = pkg.chebfd_matrix_create_lattice(kind, *L, t=1.0, m=m, W=1.3, seed=5, also_single=True)
+    gen = lattice.topi_slab_csr if kind == "topi_slab" else lattice.topi_csr
+    Ho = lattice.to_scipy(*gen(*L, t=1.0, m=m, W=1.3, seed=5))
+    mk = lambda s: torch.from_numpy(workloads.random_block(s, H.n, nb, True)).to(
+        DEV).to(torch.complex64)
+    U, W0, Y0 = mk(1), mk(2), mk(3)
+    alpha, beta, c = 0.21, 0.037, -0.43
+    ref_w = 2.0 * ofilt.apply_A(Ho, alpha, beta, U.cpu().numpy().astype(np.complex128)) \
+        - W0.cpu().numpy()
+    ref_y = Y0.cpu().numpy() + c * ref_w
+    got = {}
+    for free in (True, False):
+        H.set_matrix_free(free)
+        Wt, Yt = W0.clone(), Y0.clone()
+        pkg.chebfd_chebyshev_step(H, alpha, beta, c, U, Wt, Yt)
+        got[free] = (Wt.cpu().numpy(), Yt.cpu().numpy())
+    tol = 30 * 2.0 ** -24
+    assert rel(got[True][0], ref_w) <= tol and rel(got[True][1], ref_y) <= tol
+    assert rel(got[True][0], got[False][0]) <= 2 * tol
+
+
+def test_matrix_free_only_for_insulator_lattices():
+    g = pkg.chebfd_matrix_create_lattice("graphene", 8, 8, W=1.0, seed=1, also_single=True)
+    with pytest.raises(pkg.ChebFDError):
+        g.set_matrix_free(True)
+    t = pkg.chebfd_matrix_create_lattice("topi", 4, 4, 4, W=1.0, seed=1)   # no single copy
+    with pytest.raises(pkg.ChebFDError):
+        t.set_matrix_free(True)
+
+
+@pytest.mark.parametrize("kind,L", [("topi", (200, 160, 2)), ("topi_slab", (208, 152, 2))])
+def test_tiled_site_order_visits_every_site(kind, L):
+    """Lattices whose two x-y planes of 64-column rows exceed L2 are visited
+    in tiles of the x-y plane (200 = 8 x 25, 160 = 8 x 20, 208 = 13 x 16,
+    152 = 8 x 19): the blocked and the matrix-free steps still reproduce the
+    oracle step on every row."""
+    m = 2.0 if kind == "topi_slab" else 1.0
+    H = pkg.chebfd_matrix_create_lattice(kind, *L, t=1.0, m=m, W=0.8, seed=2, also_single=True)
+    gen = lattice.topi_slab_csr if kind == "topi_slab" else lattice.topi_csr
+    Ho = lattice.to_scipy(*gen(*L, t=1.0, m=m, W=0.8, seed=2))
+    nb = 64
+    mk = lambda s: torch.from_numpy(workloads.random_block(s, H.n, nb, True)).to(
+        DEV).to(torch.complex64)
+    U, W0, Y0 = mk(1), mk(2), mk(3)
+    alpha, beta, c = 0.2, -0.01, 0.5
+    ref_w = 2.0 * ofilt.apply_A(Ho, alpha, beta, U.cpu().numpy().astype(np.complex128)) \
+        - W0.cpu().numpy()
+    for free in (False, True):
+        H.set_matrix_free(free)
+        Wt, Yt = W0.clone(), Y0.clone()
+        pkg.chebfd_chebyshev_step(H, alpha, beta, c, U, Wt, Yt)
+        w = Wt.cpu().numpy()
+        # every row updated correctly (a skipped or doubled site shows up row-wise)
+        row_err = np.linalg.norm(w - ref_w, axis=1) / np.linalg.norm(ref_w, axis=1)
+        assert row_err.max() <= 1e-5, (free, row_err.max())
