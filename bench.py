@@ -418,17 +418,19 @@ def run_ours(args):
     pkg.chebfd_random_block(Wv, ns_total=nb, seed=12)
     Y.zero_()
 
-    def time_step(reps=50):
+    def time_step(reps=50, width=None):
+        # width < nb: the step on the first `width` columns of the same blocks
+        u_, w_, y_ = (U, Wv, Y) if width is None else (U[:, :width], Wv[:, :width], Y[:, :width])
         for _ in range(5):
-            pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, U, Wv, Y)
+            pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, u_, w_, y_)
         torch.cuda.synchronize()
         k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         k0.record(stream)
         for i in range(reps):
             if i % 2 == 0:
-                pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, U, Wv, Y)
+                pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, u_, w_, y_)
             else:
-                pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, Wv, U, Y)
+                pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, w_, u_, y_)
         k1.record(stream)
         torch.cuda.synchronize()
         return k0.elapsed_time(k1) / 1e3 / reps
@@ -457,6 +459,17 @@ def run_ours(args):
             dtype_name, nb), "launch_us": t_sell * 1e6,
             "achieved": bytes_launch / t_sell / 1e9,
             "frac": bytes_launch / t_sell / 1e9 / peaks["hbm_gbs"]}
+    # the same step at narrower block widths (strided panels of the same blocks)
+    by_width = {}
+    for width in (16, 32):
+        if width < nb and (width * S_v) % 16 == 0:
+            t_w = time_step(width=width)
+            b_w = N * (w["nnz_row"] * (S_d + 4) + 5 * width * S_v)
+            by_width[str(width)] = {"launch_us": t_w * 1e6, "achieved": b_w / t_w / 1e9,
+                                    "frac": b_w / t_w / 1e9 / peaks["hbm_gbs"]}
+    by_width[str(nb)] = {"launch_us": t_launch * 1e6, "achieved": achieved,
+                         "frac": achieved / peaks["hbm_gbs"]}
+    roof["by_block_width"] = by_width
     if single and w["kind"] == "topi":
         # matrix-free step: the insulator's entries rebuilt in registers
         H.set_matrix_free(True)
