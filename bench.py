@@ -299,12 +299,14 @@ def bench_ensemble(pkg, workloads, dev, peak_gbs):
 
 
 def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chiral=True,
-                precisions=("fp64", "mixed", "mixed_df")):
+                precisions=("fp64", "mixed", "mixed_df"), matrix_free=False):
     """Wall time of the whole ChebFD solve (Sec. 3.1 steps 4-8) to residual
     <= eps ||H|| for every accepted pair in [-delta, delta]: plain FP64 against
     the mixed forms (single-precision filter until the residuals stall, then
     FP64 or double-float sweeps; FP64 Gram, Rayleigh-Ritz and residuals
-    throughout), and the mixed double-float form with the MLP's parameters."""
+    throughout), and the mixed double-float form with the MLP's parameters,
+    with `matrix_free` once more with H's entries rebuilt in registers in
+    both the single-precision and the double-float steps."""
     import torch
     out = {}
     lams = {}
@@ -350,9 +352,16 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chir
                                                           m_feat=mlp_train.M_FEAT)
         ns_m = max(ns_m, int(np.ceil(nt / 4.0)) * 4 + 8)   # never fewer vectors than targets
         t_choose = time.perf_counter() - t0
-        run("mixed_df_mlp", ns_m, Np_m, kern_m, "mixed_df",
-            extra={"ns": ns_m, "Np": Np_m, "kernel": kern_m, "kpm_n_target": nt,
-                   "seconds_parameter_choice": t_choose}, t_pre=t_choose)
+        extra = {"ns": ns_m, "Np": Np_m, "kernel": kern_m, "kpm_n_target": nt,
+                 "seconds_parameter_choice": t_choose}
+        run("mixed_df_mlp", ns_m, Np_m, kern_m, "mixed_df", extra=extra, t_pre=t_choose)
+        if matrix_free:
+            H.set_matrix_free(True)
+            try:
+                run("mixed_df_mlp_matrix_free", ns_m, Np_m, kern_m, "mixed_df", extra=extra,
+                    t_pre=t_choose)
+            finally:
+                H.set_matrix_free(False)
     out["eps"] = eps
     out["workload"] = "%s, window [-%.6g, %.6g], n_s = %d, N_p = %d, Lanczos mu=2" % (
         label, delta, delta, ns, Np)
@@ -527,7 +536,8 @@ def run_ours(args):
             out["time_to_solution"] = bench_solve(pkg, H, a, b, delta, Np, ns, w["label"],
                                                   learned=w["kind"] == "topi",
                                                   chiral=w["kind"] == "topi",
-                                                  precisions=args.solve_precisions)
+                                                  precisions=args.solve_precisions,
+                                                  matrix_free=w["kind"] == "topi")
         except pkg.ChebFDError as e:     # reported, the throughput line still prints
             out["time_to_solution"] = {"error": str(e)}
 

@@ -173,11 +173,13 @@ chebfd_status chebfd_matrix_set_blocked(chebfd_matrix* H, int enable);
  * For an insulator lattice (TOPI or TOPI_SLAB) built with also_single and
  * sell_sigma = 1, chebfd_matrix_set_matrix_free(H, 1) makes the complex64
  * Chebyshev step (chebfd_chebyshev_step and the loop of chebfd_filter_block)
- * rebuild H's entries in registers from the lattice description (hopping
- * t/2 blocks, onsite m +- V_s with V_s regenerated from the SplitMix64
- * disorder stream) instead of reading any stored matrix: the step then moves
- * only the vectors.  The other operations keep using the stored arrays.
- * Results agree with the stored-matrix kernels to FP32 rounding.
+ * and the double-float step (the loop of chebfd_filter_block_df and of the
+ * MIXED_DF solve's sweeps) rebuild H's entries in registers from the lattice
+ * description (hopping t/2 blocks, onsite m +- V_s with V_s regenerated from
+ * the SplitMix64 disorder stream) instead of reading any stored matrix: the
+ * step then moves only the vectors.  The other operations keep using the
+ * stored arrays.  Results agree with the stored-matrix kernels to FP32
+ * (complex64) or double-float rounding.
  * (H, 0) returns to the stored matrix.  EUNSUPPORTED for other matrices. */
 chebfd_status chebfd_matrix_set_matrix_free(chebfd_matrix* H, int enable);
 

@@ -233,7 +233,8 @@ class Matrix:
                "chebfd_matrix_set_blocked")
 
     def set_matrix_free(self, enable):
-        """Rebuild the insulator's entries in registers in the complex64 step."""
+        """Rebuild the insulator's entries in registers in the complex64 step
+        and in the double-float step."""
         _check(lib().chebfd_matrix_set_matrix_free(self.handle, 1 if enable else 0),
                "chebfd_matrix_set_matrix_free")
 

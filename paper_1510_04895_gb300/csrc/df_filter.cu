@@ -17,6 +17,8 @@ void launch_step_df_c(const SellView& H, StepMode mode, const StepArgs& a, int w
 void launch_step_df_r(const SellView& H, StepMode mode, const StepArgs& a, int wc, int width,
                       int sms, cudaStream_t s);
 void validate_block(const Matrix& M, chebfd_dtype dt, const void* X, int64_t ld, int nb);
+bool stencil_df_applies(const Matrix& M, StepMode mode, int wc);
+void launch_stencil_df(const Matrix& M, const StepArgs& a, int wc, cudaStream_t s);
 
 namespace {
 
@@ -73,6 +75,7 @@ int conv_grid(int64_t work) {
 }
 
 void launch_df(const Matrix& M, StepMode mode, const StepArgs& a, int wc, cudaStream_t s) {
+    if (stencil_df_applies(M, mode, wc)) return launch_stencil_df(M, a, wc, s);
     SellView v;
     v.chunk_ptr = M.chunk_ptr;
     v.chunk_len = M.chunk_len;

@@ -16,6 +16,7 @@
 #include <cstdlib>
 
 #include "async_copy.cuh"
+#include "df.cuh"
 #include "filter_kernels.cuh"
 
 namespace chebfd {
@@ -27,6 +28,7 @@ constexpr int ST_THREADS = 256;
 struct StencilView {
     int64_t Lx, Ly, Lz, nsite;
     float h;        // t / 2
+    double hd;      // t / 2 in FP64 (double-float step)
     double m, W;
     uint64_t seed;
     int slab;       // open in z
@@ -174,6 +176,187 @@ void launch_g(const StencilView& v, const StepArgs& a, int wc, float shift, int 
     kern<<<grid, ST_THREADS, 0, s>>>(v, a, wc, shift);
 }
 
+// ---- double-float variant (the FP64-class sweep of MIXED_DF) -------------
+//
+// One lane owns one double-float complex entry (16 bytes: hi (re, im), lo
+// (re, im)) of the 4 rows; every entry of H is real or imaginary, so each is
+// one scalar-by-pair double-float multiply-add (13 per row) against two in
+// the SELL double-float kernel.  The onsite value carries the shift
+// beta/alpha (summed in FP64, then split).
+
+__device__ __forceinline__ DFPair df_pair(const float4& c) {
+    DFPair p;
+    p.hi = make_float2(c.x, c.y);
+    p.lo = make_float2(c.z, c.w);
+    return p;
+}
+// i u for a complex pair u = (re, im): (-im, re)
+__device__ __forceinline__ DFPair df_times_i(const DFPair& u) {
+    DFPair r;
+    r.hi = make_float2(-u.hi.y, u.hi.x);
+    r.lo = make_float2(-u.lo.y, u.lo.x);
+    return r;
+}
+
+template <int J>
+__device__ __forceinline__ void hop_df(DFPair* acc, const float4* g, float h1, float h2, float q) {
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        const float sd = o < 2 ? -1.f : 1.f;
+        df_mac(acc[o], sd * h1, sd * h2, df_pair(g[o]));
+        if (J == 0) {
+            df_mac(acc[o], q * h1, q * h2, df_times_i(df_pair(g[o ^ 3])));
+        } else if (J == 1) {
+            const float gi = (o == 0 || o == 2) ? q : -q;
+            df_mac(acc[o], gi * h1, gi * h2, df_pair(g[o ^ 3]));
+        } else {
+            const float gr = (o == 0 || o == 2) ? q : -q;
+            df_mac(acc[o], gr * h1, gr * h2, df_times_i(df_pair(g[o ^ 2])));
+        }
+    }
+}
+
+// a.ldg / a.ldw / a.ldy in 16-byte chunks (one double-float complex entry).
+template <int G, int MINB>
+__global__ void __launch_bounds__(ST_THREADS, MINB)
+    stencil_df_kernel(StencilView L, StepArgs a, int wc, double shift) {
+    constexpr int B = 4, SLOTS = ST_THREADS / G;
+    const int lane = threadIdx.x % G, slot = threadIdx.x / G;
+    const bool on = lane < wc;
+    const float4* __restrict__ u = reinterpret_cast<const float4*>(a.gather);
+    float4* __restrict__ w = reinterpret_cast<float4*>(a.w);
+    float4* __restrict__ y = reinterpret_cast<float4*>(a.y);
+    const int64_t ldg = a.ldg, ldw = a.ldw, ldy = a.ldy;
+    float ta1, ta2, c1, c2, h1, h2;
+    df_split(2.0 * a.alpha, ta1, ta2);
+    df_split(a.c0, c1, c2);
+    df_split(L.hd, h1, h2);
+
+    const int tile = a.tile > 0 ? a.tile : 1;
+    const int64_t wave = (int64_t)gridDim.x * tile * SLOTS;
+    const int iters = (int)((L.nsite + wave - 1) / wave) * tile;
+    const int64_t wrap = wave - (int64_t)(tile - 1) * SLOTS;
+    int64_t q = (int64_t)blockIdx.x * tile * SLOTS + slot;
+    int tt = 0;
+
+    for (int it = 0; it < iters; ++it) {
+        const int64_t q_next = tt + 1 == tile ? q + wrap : q + SLOTS;
+        if (q < L.nsite && on) {
+            const int64_t s = a.order.site(q);
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                prefetch_l2(w + (s * B + r) * ldw + lane);
+                prefetch_l2(y + (s * B + r) * ldy + lane);
+            }
+            const int si = (int)s, Lx = (int)L.Lx, Ly = (int)L.Ly;
+            const int64_t x = si % Lx, yy = (si / Lx) % Ly, z = si / (Lx * Ly);
+            auto site = [&](int64_t cx, int64_t cy, int64_t cz) {
+                return cx + L.Lx * (cy + L.Ly * cz);
+            };
+            auto gather = [&](int64_t sn, float4* g) {
+#pragma unroll
+                for (int o = 0; o < B; ++o) g[o] = __ldg(u + (sn * B + o) * ldg + lane);
+            };
+            DFPair acc[B];
+#pragma unroll
+            for (int r = 0; r < B; ++r) acc[r].hi = acc[r].lo = make_float2(0.f, 0.f);
+            float4 g[B];
+            gather(s, g);
+            const double V =
+                __dmul_rn(L.W, splitmix_uniform(L.seed, STREAM_DISORDER, (uint64_t)s) - 0.5);
+            double up, lo;
+            if (L.slab) {
+                up = __dadd_rn(V, L.m);
+                lo = __dadd_rn(V, -L.m);
+            } else {
+                up = __dadd_rn(L.m, V);
+                lo = -up;
+            }
+            float up1, up2, lo1, lo2;
+            df_split(up + shift, up1, up2);
+            df_split(lo + shift, lo1, lo2);
+#pragma unroll
+            for (int o = 0; o < B; ++o)
+                df_mac(acc[o], o < 2 ? up1 : lo1, o < 2 ? up2 : lo2, df_pair(g[o]));
+            gather(site((x + L.Lx - 1) % L.Lx, yy, z), g);
+            hop_df<0>(acc, g, h1, h2, 1.f);
+            gather(site((x + 1) % L.Lx, yy, z), g);
+            hop_df<0>(acc, g, h1, h2, -1.f);
+            gather(site(x, (yy + L.Ly - 1) % L.Ly, z), g);
+            hop_df<1>(acc, g, h1, h2, 1.f);
+            gather(site(x, (yy + 1) % L.Ly, z), g);
+            hop_df<1>(acc, g, h1, h2, -1.f);
+            if (!L.slab || z > 0) {
+                gather(site(x, yy, (z + L.Lz - 1) % L.Lz), g);
+                hop_df<2>(acc, g, h1, h2, 1.f);
+            }
+            if (!L.slab || z + 1 < L.Lz) {
+                gather(site(x, yy, (z + 1) % L.Lz), g);
+                hop_df<2>(acc, g, h1, h2, -1.f);
+            }
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                const int64_t row = s * B + r;
+                const DFPair hu = df_norm(acc[r]);
+                const DFPair wo = df_pair(__ldcs(w + row * ldw + lane));
+                DFPair wn;
+                wn.hi = df_neg(wo.hi);
+                wn.lo = df_neg(wo.lo);
+                df_mac(wn, ta1, ta2, hu);  // 2 alpha (H + beta/alpha) u - w
+                wn = df_norm(wn);
+                DFPair yn = df_pair(__ldcs(y + row * ldy + lane));
+                df_mac(yn, c1, c2, wn);
+                yn = df_norm(yn);
+                __stcs(w + row * ldw + lane, make_float4(wn.hi.x, wn.hi.y, wn.lo.x, wn.lo.y));
+                __stcs(y + row * ldy + lane, make_float4(yn.hi.x, yn.hi.y, yn.lo.x, yn.lo.y));
+            }
+        }
+        q = q_next;
+        tt = tt + 1 == tile ? 0 : tt + 1;
+    }
+}
+
+template <int G, int MINB>
+void launch_df_gm(const StencilView& v, const StepArgs& a, int wc, double shift, int sms,
+                  cudaStream_t s) {
+    auto kern = stencil_df_kernel<G, MINB>;
+    const int grid =
+        sms * std::min(8, cached_occupancy(reinterpret_cast<const void*>(kern), ST_THREADS, 0));
+    kern<<<grid, ST_THREADS, 0, s>>>(v, a, wc, shift);
+}
+
+// Resident CTAs per SM the register budget is fitted to (2, 3 or 4;
+// CHEBFD_DF_FREE_CTAS overrides the default).
+template <int G>
+void launch_df_g(const StencilView& v, const StepArgs& a, int wc, double shift, int sms,
+                 cudaStream_t s) {
+    static const int minb = [] {
+        const char* e = getenv("CHEBFD_DF_FREE_CTAS");
+        return e ? std::min(4, std::max(2, atoi(e))) : 4;
+    }();
+    if (minb == 4)
+        launch_df_gm<G, 4>(v, a, wc, shift, sms, s);
+    else if (minb == 3)
+        launch_df_gm<G, 3>(v, a, wc, shift, sms, s);
+    else
+        launch_df_gm<G, 2>(v, a, wc, shift, sms, s);
+}
+
+StencilView view_of_gen(const Matrix& M) {
+    StencilView v;
+    v.Lx = M.gen.Lx;
+    v.Ly = M.gen.Ly;
+    v.Lz = M.gen.Lz;
+    v.nsite = v.Lx * v.Ly * v.Lz;
+    v.h = (float)(M.gen.t / 2.0);
+    v.hd = M.gen.t / 2.0;
+    v.m = M.gen.m;
+    v.W = M.gen.W;
+    v.seed = M.gen.seed;
+    v.slab = M.gen.kind == CHEBFD_LATTICE_TOPI_SLAB ? 1 : 0;
+    return v;
+}
+
 }  // namespace
 
 bool stencil_step_applies(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs& a,
@@ -183,16 +366,7 @@ bool stencil_step_applies(const Matrix& M, chebfd_dtype dt, StepMode mode, const
 }
 
 void launch_stencil_step(const Matrix& M, const StepArgs& a, int wc, cudaStream_t s) {
-    StencilView v;
-    v.Lx = M.gen.Lx;
-    v.Ly = M.gen.Ly;
-    v.Lz = M.gen.Lz;
-    v.nsite = v.Lx * v.Ly * v.Lz;
-    v.h = (float)(M.gen.t / 2.0);
-    v.m = M.gen.m;
-    v.W = M.gen.W;
-    v.seed = M.gen.seed;
-    v.slab = M.gen.kind == CHEBFD_LATTICE_TOPI_SLAB ? 1 : 0;
+    const StencilView v = view_of_gen(M);
     StepArgs b = a;
     static const int env_tile = [] {
         const char* e = getenv("CHEBFD_BELL_TILE");
@@ -208,6 +382,29 @@ void launch_stencil_step(const Matrix& M, const StepArgs& a, int wc, cudaStream_
         launch_g<8>(v, b, wc, shift, M.num_sms, s);
     else
         launch_g<4>(v, b, wc, shift, M.num_sms, s);
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+}
+
+// Double-float matrix-free step (MODE_STEP) for the double-float filter.
+bool stencil_df_applies(const Matrix& M, StepMode mode, int wc) {
+    return M.stencil_enabled && M.has_gen && M.complex_values && mode == MODE_STEP && wc >= 1 &&
+           wc <= 32;
+}
+
+void launch_stencil_df(const Matrix& M, const StepArgs& a, int wc, cudaStream_t s) {
+    const StencilView v = view_of_gen(M);
+    StepArgs b = a;
+    b.tile = 1;
+    b.order = site_order_of(M, wc);
+    const double shift = a.beta / a.alpha;
+    if (wc > 16)
+        launch_df_g<32>(v, b, wc, shift, M.num_sms, s);
+    else if (wc > 8)
+        launch_df_g<16>(v, b, wc, shift, M.num_sms, s);
+    else if (wc > 4)
+        launch_df_g<8>(v, b, wc, shift, M.num_sms, s);
+    else
+        launch_df_g<4>(v, b, wc, shift, M.num_sms, s);
     CHEBFD_CHECK_CUDA(cudaGetLastError());
 }
 

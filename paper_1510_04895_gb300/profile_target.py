@@ -5,8 +5,9 @@
         64x64x32x4 insulator, N = 524288; graphene: the 1024x1024 honeycomb
         lattice, N = 2097152); `sell` bypasses the insulator's blocked copy,
         `free` runs the matrix-free step.
-    python -m paper_1510_04895_gb300.profile_target df [n_b]
-        one double-float filter of degree 8 on the insulator (n_b columns).
+    python -m paper_1510_04895_gb300.profile_target df [n_b] [free]
+        one double-float filter of degree 8 on the insulator (n_b columns);
+        `free` runs its step matrix-free.
     python -m paper_1510_04895_gb300.profile_target solve [fp64|mixed_df]
         one ChebFD iteration (filter of degree 20, SVQB + Rayleigh-Ritz) on a
         32x32x32x4 insulator (N = 131072, W = 1, seed 1) with n_s = 256: the
@@ -29,6 +30,8 @@ H = pkg.chebfd_matrix_create_lattice(w["kind"], w["Lx"], w["Ly"], w.get("Lz", 1)
                                      m=w.get("m", 0.0), W=w["W"], seed=w["seed"], also_single=True)
 if kind == "df":
     nb = int(sys.argv[2]) if len(sys.argv) > 2 else 32
+    if len(sys.argv) > 3 and sys.argv[3] == "free":
+        H.set_matrix_free(True)
     X = torch.empty((H.n, nb), dtype=torch.complex128, device="cuda")
     pkg.chebfd_random_block(X, ns_total=nb, seed=1)
     gc = pkg.chebfd_window_coeffs(-4.3, 4.3, -0.1, 0.1, 8, "lanczos", 2.0)

@@ -115,3 +115,24 @@ def test_df_filter_slab_blocked_and_sell(blocked):
     Ho = lattice.to_scipy(*lattice.topi_slab_csr(5, 6, 4, t=1.0, m=2.0, W=2.0, seed=2))
     got, ref = _df_case(H, Ho, 40, 90, "lanczos", (-0.06, 0.06))
     assert rel(got, ref) <= 1e-11, rel(got, ref)
+
+
+@pytest.mark.parametrize("kind,L,t,nb", [("topi", (6, 5, 4), 1.0, 40), ("topi", (2, 3, 2), 0.7, 3),
+                                         ("topi_slab", (5, 6, 4), 1.1, 32),
+                                         ("topi_slab", (4, 4, 1), 1.0, 17)])
+def test_df_filter_matrix_free(kind, L, t, nb):
+    """The double-float step with H's entries rebuilt in registers (hopping
+    t/2 split into hi + lo, onsite + beta/alpha summed in FP64 and split):
+    within 1e-11 of the oracle and of the stored-matrix double-float filter,
+    on both lattices, a ragged second panel and edges 1-2 (coinciding
+    neighbours); t = 0.7, 1.1 have no exact float."""
+    m = 2.0 if kind == "topi_slab" else 1.0
+    H = pkg.chebfd_matrix_create_lattice(kind, *L, t=t, m=m, W=1.3, seed=4, also_single=True)
+    gen = lattice.topi_slab_csr if kind == "topi_slab" else lattice.topi_csr
+    Ho = lattice.to_scipy(*gen(*L, t=t, m=m, W=1.3, seed=4))
+    H.set_matrix_free(True)
+    got, ref = _df_case(H, Ho, nb, 60, "lanczos", (-0.08, 0.08))
+    assert rel(got, ref) <= 1e-11, rel(got, ref)
+    H.set_matrix_free(False)
+    stored, _ = _df_case(H, Ho, nb, 60, "lanczos", (-0.08, 0.08))
+    assert rel(got, stored) <= 1e-11, rel(got, stored)
