@@ -36,6 +36,14 @@ def test_splitmix64_known_answers():
     assert got == want
 
 
+def test_uniform_is_the_top_53_bits():
+    """u = (word >> 11) 2^-53 on the published SplitMix64 outputs, in exact
+    integer arithmetic."""
+    want = [int(r[0], 16) for r in _rows("splitmix64_seed0.txt")]
+    got = rng.uniform(0, 0, np.arange(len(want)))
+    assert [float(x) for x in got] == [(w >> 11) / 2.0 ** 53 for w in want]
+
+
 def test_uniform_range_and_streams_differ():
     u = rng.uniform(7, 0, np.arange(10000))
     assert u.min() >= 0.0 and u.max() < 1.0
@@ -63,9 +71,13 @@ def test_window_coefficients_match_defining_integral(window):
         assert abs(c[n] - ref) < 1e-10, (n, c[n], ref)
 
 
-def test_scaling_maps_interval():
-    alpha, beta = coeffs.scaling(-5.5, 5.5)
-    assert alpha * -5.5 + beta == pytest.approx(-1.0) and alpha * 5.5 + beta == pytest.approx(1.0)
+@pytest.mark.parametrize("a,b", [(-5.5, 5.5), (-2.0, 3.0), (0.5, 7.25), (-9.0, -1.0)])
+def test_scaling_maps_interval(a, b):
+    """alpha a + beta = -1 and alpha b + beta = 1 (Sec. 2.1), on symmetric and
+    shifted intervals (beta = 0 only for the symmetric one)."""
+    alpha, beta = coeffs.scaling(a, b)
+    assert alpha * a + beta == pytest.approx(-1.0, abs=1e-15)
+    assert alpha * b + beta == pytest.approx(1.0, abs=1e-15)
 
 
 def test_kernel_factors_special_values():
