@@ -16,6 +16,10 @@ Readings of the paper taken here (the paper leaves them open):
   factor per iteration, so it would have been accepted;
 * restart (step 8b): the next search block is the full set of Ritz vectors,
   which spans the same space as the orthonormalised filtered block;
+* extraction="harmonic" replaces step 7's Ritz pairs by harmonic Ritz pairs
+  for the target tau = (lam_lo + lam_hi) / 2 (rr.harmonic_ritz): window
+  membership, ghosts and convergence then use their Rayleigh quotients and
+  residuals, and the restart block is the set of harmonic vectors;
 * search vectors (step 4): SplitMix64 stream 1, column k of n_s, entry 2u-1 at
   word index i*n_s + k (real) or 2(i*n_s + k) + {0, 1} (complex parts).
 """
@@ -34,7 +38,7 @@ def search_vectors(seed, D, ns, complex_values):
 
 
 def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
-           max_iter=40, filter_fn=None, X0=None, complex_values=None):
+           max_iter=40, filter_fn=None, X0=None, complex_values=None, extraction="ritz"):
     """Run ChebFD; returns a dict with the accepted pairs and the iteration log.
 
     ``filter_fn(X)``, when given, replaces the recurrence of Fig. ChebFD by
@@ -54,7 +58,10 @@ def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
     for it in range(1, max_iter + 1):
         Y = filter_fn(X) if filter_fn is not None else filt.filter_block(H, alpha, beta, gc, X)
         Q, rank, refill = svqb.svqb(Y, seed=seed, refill_counter=refill)
-        theta, V, res = rr.rayleigh_ritz(H, Q)
+        if extraction == "harmonic":
+            theta, V, res, _ = rr.harmonic_ritz(H, Q, 0.5 * (lam_lo + lam_hi))
+        else:
+            theta, V, res = rr.rayleigh_ritz(H, Q)
         inwin = (theta >= lam_lo) & (theta <= lam_hi)
         ghost = np.zeros_like(inwin)
         if prev is not None:

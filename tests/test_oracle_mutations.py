@@ -15,6 +15,7 @@ tests instead.
 """
 import numpy as np
 import pytest
+import scipy.linalg
 
 import test_oracle_pins as pins
 from oracle import coeffs, filter as filt, kpm, lattice, mlp, quality, rng, rr, sell, svqb
@@ -125,6 +126,18 @@ class _NumpyArgsort:
 
     def argsort(self, a, kind=None):
         return self._argsort(np.asarray(a))
+
+
+def _harmonic_unnormalised(orig):
+    def f(H, Y, tau):
+        HY = H @ Y
+        Z = HY - tau * Y
+        mu, S = scipy.linalg.eigh(Y.conj().T @ Z, Z.conj().T @ Z)
+        V, HV = Y @ S, HY @ S
+        rho = np.real(np.sum(V.conj() * HV, axis=0))
+        o = np.argsort(rho)
+        return rho[o], V[:, o], np.linalg.norm(HV - V * rho[None, :], axis=0)[o], tau + 1.0 / mu[o]
+    return f
 
 
 def _mix64_shift(orig):
@@ -261,6 +274,13 @@ MUTANTS = {
     "Ritz vectors not rotated (V = Y)": (
         _wrap(rr, "rayleigh_ritz", _rr(rotate=False)),
         [pins.test_rayleigh_ritz_exact_on_invariant_subspace]),
+    "harmonic Ritz values tau - 1/mu": (
+        _wrap(rr, "harmonic_ritz", lambda o: lambda H, Y, tau: (
+            lambda r: (r[0], r[1], r[2], 2.0 * tau - r[3]))(o(H, Y, tau))),
+        [pins.test_harmonic_values_are_inverse_ritz_values_of_the_shifted_inverse]),
+    "harmonic vectors left K-normalised": (
+        _wrap(rr, "harmonic_ritz", _harmonic_unnormalised),
+        [pins.test_harmonic_ritz_exact_on_invariant_subspace]),
     "KPM moments without 1/R": (
         _wrap(kpm, "moments", lambda o: lambda H, alpha, beta, M, R, seed, complex_values:
               o(H, alpha, beta, M, R, seed, complex_values) * R),

@@ -415,6 +415,37 @@ def test_rayleigh_ritz_exact_on_invariant_subspace():
     assert np.allclose(res, rr.residual_norms(H, Vr, theta), atol=1e-13)
 
 
+def test_harmonic_ritz_exact_on_invariant_subspace():
+    """On an invariant subspace the harmonic vectors are eigenvectors: Rayleigh
+    quotients and harmonic values both equal the eigenvalues, residuals vanish."""
+    H = lattice.to_scipy(*lattice.topi_csr(3, 3, 3, W=0.8, seed=9))
+    lam, V = np.linalg.eigh(H.toarray())
+    rs = np.random.default_rng(4)
+    M = np.linalg.qr(rs.standard_normal((10, 10)) + 1j * rs.standard_normal((10, 10)))[0]
+    Y = V[:, 50:60] @ M
+    rho, Vh, res, theta_h = rr.harmonic_ritz(H, Y, 0.5 * (lam[50] + lam[59]) + 1e-3)
+    assert np.allclose(rho, lam[50:60], atol=1e-12)
+    assert np.allclose(np.sort(theta_h), lam[50:60], atol=1e-10)
+    assert res.max() < 1e-12
+    assert np.allclose(np.linalg.norm(Vh, axis=0), 1.0)
+
+
+def test_harmonic_values_are_inverse_ritz_values_of_the_shifted_inverse():
+    """Harmonic Ritz values of H on span(Y) for target tau are tau + 1/mu with
+    mu the Ritz values of (H - tau)^-1 on span((H - tau) Y) (Morgan 1991):
+    checked against a dense inverse and an independent orthonormal basis."""
+    H = lattice.to_scipy(*lattice.topi_csr(2, 3, 2, W=1.1, seed=3)).toarray()
+    n = H.shape[0]
+    rs = np.random.default_rng(6)
+    Y = np.linalg.qr(rs.standard_normal((n, 7)) + 1j * rs.standard_normal((n, 7)))[0]
+    tau = 0.137
+    _, _, _, theta_h = rr.harmonic_ritz(H, Y, tau)
+    Q = np.linalg.qr((H - tau * np.eye(n)) @ Y)[0]
+    B = Q.conj().T @ np.linalg.inv(H - tau * np.eye(n)) @ Q
+    mu = np.linalg.eigvalsh(0.5 * (B + B.conj().T))
+    assert np.allclose(np.sort(theta_h), np.sort(tau + 1.0 / mu), rtol=1e-9, atol=1e-9)
+
+
 # ---------------------------------------------------------------- whole iteration
 
 
@@ -455,6 +486,23 @@ def test_chebfd_small_topi_against_dense():
 
 
 # ---------------------------------------------------------------- MLP reference
+
+
+def test_chebfd_harmonic_extraction_small_topi_against_dense():
+    """Harmonic Ritz extraction (Sec. 6) on the smallest insulator workload:
+    the same window eigenvalues as dense diagonalisation, residuals <= 1e-9
+    ||H||, in no more iterations than ordinary Ritz pairs."""
+    H = lattice.to_scipy(*lattice.topi_csr(8, 8, 8, t=1.0, m=1.0, W=0.5, seed=0))
+    a, b = bounds.lanczos_bounds(H, 30, seed=0)
+    e = np.linalg.eigvalsh(H.toarray())
+    ew = e[np.abs(e) <= 0.1]
+    r = solve.chebfd(H, a, b, -0.1, 0.1, 64, 200, 1e-9, kind="jackson", seed=0,
+                     extraction="harmonic")
+    assert r["converged"] and len(r["theta"]) == len(ew)
+    assert np.abs(np.sort(r["theta"]) - ew).max() <= 1e-10 * r["normH"]
+    assert r["res"].max() <= 1e-9 * r["normH"]
+    ritz = solve.chebfd(H, a, b, -0.1, 0.1, 64, 200, 1e-9, kind="jackson", seed=0)
+    assert r["iterations"] <= ritz["iterations"]
 
 
 def test_mlp_gradient_matches_central_differences():
