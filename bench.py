@@ -306,16 +306,17 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chir
     FP64 or double-float sweeps; FP64 Gram, Rayleigh-Ritz and residuals
     throughout), and the mixed double-float form with the MLP's parameters,
     with `matrix_free` once more with H's entries rebuilt in registers in
-    both the single-precision and the double-float steps."""
+    both the single-precision and the double-float steps, and that once more
+    with harmonic Ritz pairs for the window centre (Sec. 6)."""
     import torch
     out = {}
     lams = {}
 
-    def run(name, ns_r, Np_r, kern, prec, extra=None, t_pre=0.0):
+    def run(name, ns_r, Np_r, kern, prec, extra=None, t_pre=0.0, extraction="ritz"):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = pkg.chebfd_solve(H, -delta, delta, ns_r, Np_r, eps=eps, kernel=kern, precision=prec,
-                             a=a, b=b, max_iter=40, seed=0)
+                             a=a, b=b, max_iter=40, seed=0, extraction=extraction)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0 + t_pre
         normH = max(abs(r["a"]), abs(r["b"]))
@@ -360,6 +361,11 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chir
             try:
                 run("mixed_df_mlp_matrix_free", ns_m, Np_m, kern_m, "mixed_df", extra=extra,
                     t_pre=t_choose)
+                try:
+                    run("mixed_df_mlp_matrix_free_harmonic", ns_m, Np_m, kern_m, "mixed_df",
+                        extra=extra, t_pre=t_choose, extraction="harmonic")
+                except pkg.ChebFDError as e:     # reported; the other forms stand
+                    out["mixed_df_mlp_matrix_free_harmonic"] = {"error": str(e)}
             finally:
                 H.set_matrix_free(False)
     out["eps"] = eps

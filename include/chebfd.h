@@ -332,6 +332,23 @@ chebfd_status chebfd_rayleigh_ritz(const chebfd_matrix* H, void* Y, int64_t ld, 
                                    chebfd_dtype vdt, double* theta, double* res, void* HV,
                                    void* stream);
 
+/* Harmonic Ritz extraction (the alternative to step 7 named in Sec. 3.1 and
+ * Sec. 6; Morgan 1991, Paige-Parlett-van der Vorst 1995) on an ORTHONORMAL
+ * device block Y (N x ns, ld, R64/C128) for the target tau (e.g. the window
+ * centre): with Z = (H - tau) Y, the Hermitian-definite problem
+ * (Y^H Z) s = mu (Z^H Z) s (cuSOLVER, FP64) gives the harmonic Ritz values
+ * tau + 1/mu.  In place Y <- the unit harmonic vectors v_k = Y s_k / ||s_k||
+ * in ascending order of their Rayleigh quotients theta[k] = v_k^H H v_k
+ * (HOST, ns), res[k] = ||H v_k - theta_k v_k|| (HOST, ns, may be NULL),
+ * formed from Z and Y without a further product with H.  The vectors are
+ * unit but not orthogonal.  If Z^H Z is singular (a column of Y is an exact
+ * eigenvector at tau) the ordinary Ritz pairs are returned instead.  EINVAL
+ * for a non-finite tau or the block errors of chebfd_rayleigh_ritz.
+ * Synchronizes. */
+chebfd_status chebfd_harmonic_ritz(const chebfd_matrix* H, void* Y, int64_t ld, int ns,
+                                   chebfd_dtype vdt, double tau, double* theta, double* res,
+                                   void* stream);
+
 /* res[k] = ||H v_k - theta_k v_k|| (FP64) for the k device vectors V (N x k,
  * ld, R64/C128) and HOST theta[k]; res is a HOST array.  One product with H,
  * per-column sums reduced in a fixed order.  Synchronizes. */
@@ -466,6 +483,15 @@ typedef enum chebfd_precision {
                                    double-float filter (chebfd_filter_block_df) */
 } chebfd_precision;
 
+/* Bits of chebfd_params.flags. */
+typedef enum chebfd_solve_flags {
+    CHEBFD_SOLVE_HARMONIC = 1 /* step 7 with harmonic Ritz pairs for the target
+                                 tau = (lam_lo + lam_hi)/2 (chebfd_harmonic_ritz):
+                                 window test, ghosts and convergence use their
+                                 Rayleigh quotients and residuals; the restart
+                                 block is the set of harmonic vectors */
+} chebfd_solve_flags;
+
 /* Parameters of chebfd_solve.  Zero / negative fields take the defaults given. */
 typedef struct chebfd_params {
     double lam_lo, lam_hi;   /* target interval I_T (closed) */
@@ -479,7 +505,8 @@ typedef struct chebfd_params {
     int32_t precision;       /* chebfd_precision */
     int32_t max_iter;        /* default 50 */
     int32_t lanczos_steps;   /* default 30 */
-    int32_t reserved;
+    int32_t flags;           /* chebfd_solve_flags (0: ordinary Ritz pairs); EINVAL for
+                                unknown bits; chebfd_solve_batched takes 0 only */
     uint64_t seed;           /* search-vector / refill / Lanczos seed */
 } chebfd_params;
 

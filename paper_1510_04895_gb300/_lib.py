@@ -88,6 +88,8 @@ SIGNATURES = {
                                              ctypes.c_int, ctypes.c_uint64, c_i64p, c_i32p, c_vp]),
     "chebfd_rayleigh_ritz": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int64, ctypes.c_int,
                                             ctypes.c_int, c_dp, c_dp, c_vp, c_vp]),
+    "chebfd_harmonic_ritz": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int64, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_double, c_dp, c_dp, c_vp]),
     "chebfd_residuals": (ctypes.c_int, [c_vp, c_vp, c_dp, ctypes.c_int64, ctypes.c_int,
                                         ctypes.c_int, c_dp, c_vp]),
     "chebfd_convert_block": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int64, c_vp,
@@ -140,7 +142,7 @@ class Params(ctypes.Structure):
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("mu", ctypes.c_double),
                 ("ns", ctypes.c_int32), ("Np", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("nb", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32),
-                ("lanczos_steps", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("lanczos_steps", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
 
 
@@ -384,6 +386,18 @@ def chebfd_rayleigh_ritz(H, Y, HV=None, stream=None):
     return theta, res
 
 
+def chebfd_harmonic_ritz(H, Y, tau, stream=None):
+    """In place: Y (orthonormal) <- unit harmonic Ritz vectors for the target
+    tau; returns (Rayleigh quotients, residuals) as numpy arrays."""
+    ns = Y.shape[1]
+    theta = np.zeros(ns)
+    res = np.zeros(ns)
+    _check(lib().chebfd_harmonic_ritz(H.handle, _ptr(Y), Y.stride(0), ns, dtype_of(Y), float(tau),
+                                      theta.ctypes.data_as(c_dp), res.ctypes.data_as(c_dp),
+                                      _stream(stream)), "chebfd_harmonic_ritz")
+    return theta, res
+
+
 def chebfd_residuals(H, V, theta, stream=None):
     k = V.shape[1]
     theta = np.ascontiguousarray(theta, np.float64)
@@ -401,15 +415,19 @@ def chebfd_convert_block(X, Y, stream=None):
            "chebfd_convert_block")
 
 
+EXTRACTION = {"ritz": 0, "harmonic": 1}
+
+
 def chebfd_solve(H, lam_lo, lam_hi, ns, Np, eps=1e-9, kernel="lanczos", mu=2.0, nb=0,
                  precision="fp64", max_iter=50, seed=0, a=0.0, b=0.0, lanczos_steps=30,
-                 stream=None):
-    """Run ChebFD; returns a dict with lambda, res (numpy), V (torch, device) and the log."""
+                 stream=None, extraction="ritz"):
+    """Run ChebFD; returns a dict with lambda, res (numpy), V (torch, device) and the log.
+    extraction="harmonic" uses harmonic Ritz pairs for the window centre."""
     import torch
     p = Params(lam_lo=lam_lo, lam_hi=lam_hi, eps=eps, a=a, b=b, mu=mu, ns=ns, Np=Np,
                kernel=KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel), nb=nb,
                precision=PRECISION[precision], max_iter=max_iter,
-               lanczos_steps=lanczos_steps, reserved=0, seed=seed)
+               lanczos_steps=lanczos_steps, flags=EXTRACTION[extraction], seed=seed)
     h = c_vp()
     st = lib().chebfd_solve(H.handle, ctypes.byref(p), _stream(stream), ctypes.byref(h))
     if st not in (0, 5) or not h:
@@ -537,7 +555,7 @@ def chebfd_solve_batched(E, matrices, a, b, lam_lo, lam_hi, ns, Np, eps=1e-9, ke
     p = Params(lam_lo=lam_lo, lam_hi=lam_hi, eps=eps, a=0.0, b=0.0, mu=mu, ns=ns, Np=Np,
                kernel=KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel), nb=0,
                precision=PRECISION[precision], max_iter=max_iter, lanczos_steps=0,
-               reserved=0, seed=seed)
+               flags=0, seed=seed)
     outs = (c_vp * cnt)()
     its = ctypes.c_int32()
     _check(lib().chebfd_solve_batched(E.handle, arr, a.ctypes.data_as(c_dp),

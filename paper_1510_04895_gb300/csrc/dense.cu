@@ -319,6 +319,38 @@ void heev(Handles& h, bool cplx, double* A, int ns, double* w, cudaStream_t s) {
     CHEBFD_REQUIRE(hinfo == 0, CHEBFD_ENUMERIC, "dense eigensolver did not converge");
 }
 
+// Hermitian-definite generalized eigensolve A x = mu B x (lower triangles;
+// A <- vectors normalised to x^H B x = 1, B <- its Cholesky factor, mu
+// ascending).  Returns false when B is not positive definite.
+bool hegv(Handles& h, bool cplx, double* A, double* B, int ns, double* w, cudaStream_t s) {
+    int lwork = 0;
+    if (cplx)
+        CHEBFD_CHECK_CUSOLVER(cusolverDnZhegvd_bufferSize(
+            h.solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, ns,
+            (cuDoubleComplex*)A, ns, (cuDoubleComplex*)B, ns, w, &lwork));
+    else
+        CHEBFD_CHECK_CUSOLVER(cusolverDnDsygvd_bufferSize(
+            h.solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, ns,
+            A, ns, B, ns, w, &lwork));
+    Buf work((size_t)std::max(lwork, 1) * (cplx ? 16 : 8), s);
+    Buf info(sizeof(int), s);
+    if (cplx)
+        CHEBFD_CHECK_CUSOLVER(cusolverDnZhegvd(
+            h.solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, ns,
+            (cuDoubleComplex*)A, ns, (cuDoubleComplex*)B, ns, w, work.as<cuDoubleComplex>(),
+            lwork, info.as<int>()));
+    else
+        CHEBFD_CHECK_CUSOLVER(cusolverDnDsygvd(
+            h.solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, ns, A,
+            ns, B, ns, w, work.as<double>(), lwork, info.as<int>()));
+    int hinfo = 0;
+    CHEBFD_CHECK_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (hinfo > ns) return false;  // leading minor of B not positive definite
+    CHEBFD_REQUIRE(hinfo == 0, CHEBFD_ENUMERIC, "generalized eigensolver did not converge");
+    return true;
+}
+
 void copy_block(void* dst, int64_t ldd, const void* src, int64_t lds, int64_t n, int w,
                 size_t es, cudaStream_t s) {
     CHEBFD_CHECK_CUDA(cudaMemcpy2DAsync(dst, ldd * es, src, lds * es, (size_t)w * es, n,
@@ -476,6 +508,112 @@ void gemm_small(Handles& h, bool cplx, bool ah, int ns, const double* A, const d
 
 }  // namespace
 
+// Harmonic Ritz extraction (the alternative to step 7 named in Sec. 3.1 and
+// Sec. 6; Morgan 1991, Paige-Parlett-van der Vorst 1995) on an orthonormal
+// FP64 block Y, target tau.  Z = (H - tau) Y through the fused kernel;
+// A = Y^H Z and K = Z^H Z (stored conjugated, like every small matrix here);
+// A s = mu K s with K positive definite gives the harmonic values tau + 1/mu.
+// Each harmonic vector v = Y s / ||s|| gets its Rayleigh quotient
+// rho = tau + mu / ||s||^2 (s^H A s = mu for K-normalised s) and the residual
+// ||Z s - (rho - tau) Y s|| / ||s|| = ||H v - rho v||.  In place: Y <- unit
+// harmonic vectors, ascending rho; theta_host <- rho.  When K is singular (a
+// column of Y is an exact eigenvector at tau) this falls back to the Ritz
+// pairs of A + tau.  tall_gram(X, W, C): C = conj(W^H X); tall_gemm(r, E, X, T):
+// T = X conj(E).
+template <class Gram, class Gemm>
+void harmonic_extract(const Matrix& M, double* Y, int64_t ld, int ns, bool cplx, double tau,
+                      Handles& h, Gram&& tall_gram, Gemm&& tall_gemm, double* theta_host,
+                      double* res_host, cudaStream_t s) {
+    const size_t es = cplx ? 16 : 8;
+    const int64_t n = M.n;
+    const int ew = cplx ? 2 : 1;  // doubles per entry
+    Buf Z((size_t)n * ld * es, s), T((size_t)n * ld * es, s), A((size_t)ns * ns * es, s),
+        A0((size_t)ns * ns * es, s), K((size_t)ns * ns * es, s), w((size_t)ns * sizeof(double), s),
+        dth((size_t)ns * sizeof(double), s), res((size_t)ns * sizeof(double), s);
+    spmv_impl(M, 1.0, -tau, Y, Z.p, ld, ns, cplx ? CHEBFD_C128 : CHEBFD_R64, s);
+    tall_gram(Z.as<double>(), Y, A.as<double>());
+    tall_gram(Z.as<double>(), Z.as<double>(), K.as<double>());
+    if (cplx) {
+        hermitize_kernel<true><<<grid1d((int64_t)ns * ns), 256, 0, s>>>(A.as<double>(), ns);
+        hermitize_kernel<true><<<grid1d((int64_t)ns * ns), 256, 0, s>>>(K.as<double>(), ns);
+    } else {
+        hermitize_kernel<false><<<grid1d((int64_t)ns * ns), 256, 0, s>>>(A.as<double>(), ns);
+        hermitize_kernel<false><<<grid1d((int64_t)ns * ns), 256, 0, s>>>(K.as<double>(), ns);
+    }
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+    CHEBFD_CHECK_CUDA(cudaMemcpyAsync(A0.p, A.p, (size_t)ns * ns * es, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> hw(ns), E((size_t)ns * ns * ew), nrm(ns, 1.0), rho(ns);
+    const bool definite = hegv(h, cplx, A.as<double>(), K.as<double>(), ns, w.as<double>(), s);
+    double* Ev = A.as<double>();
+    if (!definite) {
+        // Ritz pairs of A + tau = Y^H H Y instead
+        CHEBFD_CHECK_CUDA(cudaMemcpyAsync(E.data(), A0.p, (size_t)ns * ns * es,
+                                          cudaMemcpyDeviceToHost, s));
+        CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < ns; ++i) E[(size_t)ew * ((size_t)i * ns + i)] += tau;
+        CHEBFD_CHECK_CUDA(cudaMemcpyAsync(A0.p, E.data(), (size_t)ns * ns * es,
+                                          cudaMemcpyHostToDevice, s));
+        heev(h, cplx, A0.as<double>(), ns, w.as<double>(), s);
+        Ev = A0.as<double>();
+    }
+    CHEBFD_CHECK_CUDA(cudaMemcpyAsync(hw.data(), w.p, ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CHEBFD_CHECK_CUDA(cudaMemcpyAsync(E.data(), Ev, (size_t)ns * ns * es, cudaMemcpyDeviceToHost, s));
+    CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < ns; ++k) {
+        if (definite) {
+            double q = 0.0;
+            for (int i = 0; i < ns * ew; ++i) q += E[(size_t)k * ns * ew + i] * E[(size_t)k * ns * ew + i];
+            nrm[k] = std::sqrt(q);
+            rho[k] = tau + hw[k] / q;
+        } else {
+            rho[k] = hw[k];
+        }
+    }
+    std::vector<int> order(ns);
+    for (int k = 0; k < ns; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return rho[x] < rho[y]; });
+    std::vector<double> En((size_t)ns * ns * ew), dh(ns);
+    for (int j = 0; j < ns; ++j) {
+        const int k = order[j];
+        const double f = nrm[k] > 0.0 ? 1.0 / nrm[k] : 0.0;
+        for (int i = 0; i < ns * ew; ++i)
+            En[(size_t)j * ns * ew + i] = E[(size_t)k * ns * ew + i] * f;
+        theta_host[j] = rho[k];
+        dh[j] = rho[k] - tau;
+    }
+    CHEBFD_CHECK_CUDA(cudaMemcpyAsync(A.p, En.data(), (size_t)ns * ns * es, cudaMemcpyHostToDevice, s));
+    CHEBFD_CHECK_CUDA(cudaMemcpyAsync(dth.p, dh.data(), ns * sizeof(double), cudaMemcpyHostToDevice, s));
+    // V = Y conj(En) into T, Z conj(En) into Y, residuals, Y <- V
+    tall_gemm(ns, A.as<double>(), Y, T.as<double>());
+    tall_gemm(ns, A.as<double>(), Z.as<double>(), Y);
+    residuals_from_blocks(cplx, Y, T.as<double>(), dth.as<double>(), n, ld, ns, res.as<double>(), s);
+    copy_block(Y, ld, T.p, ld, n, ns, es, s);
+    if (res_host)
+        CHEBFD_CHECK_CUDA(cudaMemcpyAsync(res_host, res.p, ns * sizeof(double),
+                                          cudaMemcpyDeviceToHost, s));
+    CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+}
+
+void harmonic_ritz_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype dt, double tau,
+                        double* theta_host, double* res_host, cudaStream_t s) {
+    check_fp64_block(dt, Yv, M.n, ns, ld);
+    CHEBFD_REQUIRE(theta_host != nullptr, CHEBFD_EINVAL, "null theta");
+    CHEBFD_REQUIRE(std::isfinite(tau), CHEBFD_EINVAL, "tau must be finite");
+    const bool cplx = dt == CHEBFD_C128;
+    CHEBFD_REQUIRE(cplx == M.complex_values, CHEBFD_EINVAL, "dtype does not match the matrix");
+    const int64_t n = M.n;
+    Handles& h = handles_for_current_device(s);
+    auto gram_blas = [&](const double* X, const double* W, double* C) {
+        gemm_nh(h, cplx, ns, n, X, ld, W, ld, C, ns);
+    };
+    auto gemm_blas = [&](int r, const double* E, const double* X, double* T) {
+        gemm_ch(h, cplx, r, n, ns, E, ns, X, ld, T, ld);
+    };
+    harmonic_extract(M, (double*)Yv, ld, ns, cplx, tau, h, gram_blas, gemm_blas, theta_host,
+                     res_host, s);
+}
+
 // Steps 6-7 of Sec. 3.1 in one pass over the dense work: two SVQB passes and
 // the Rayleigh-Ritz projection, with the second SVQB transform folded into
 // the projection instead of applied to the block.  With Y1 = Y T1 (pass 1,
@@ -488,9 +626,11 @@ void gemm_small(Handles& h, bool cplx, bool ah, int ns, const double* A, const d
 // falls back to the separate calls.  Y <- Ritz vectors (ascending theta).
 // df: the six tall products in double-float arithmetic (df_dense.cu) instead
 // of cuBLAS FP64; the n_s x n_s steps stay FP64.
+// harmonic: harmonic Ritz pairs for the target tau (harmonic_extract) in the
+// orthonormal basis Y2 = Y1 T2, formed explicitly, instead of Ritz pairs.
 void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype dt, uint64_t seed,
                    int64_t* refill_counter, double* theta_host, double* res_host, bool df,
-                   cudaStream_t s) {
+                   bool harmonic, double tau, cudaStream_t s) {
     check_fp64_block(dt, Yv, M.n, ns, ld);
     const bool cplx = dt == CHEBFD_C128;
     CHEBFD_REQUIRE(cplx == M.complex_values, CHEBFD_EINVAL, "dtype does not match the matrix");
@@ -565,7 +705,20 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
         T.reset();
         if (refill_counter) *refill_counter = counter;
         orthonormalize_impl(Y, n, ns, ld, dt, seed, refill_counter, nullptr, s);
-        rayleigh_ritz_impl(M, Y, ld, ns, dt, theta_host, res_host, nullptr, s);
+        if (harmonic)
+            harmonic_extract(M, Y, ld, ns, cplx, tau, h, tall_gram, tall_gemm, theta_host,
+                             res_host, s);
+        else
+            rayleigh_ritz_impl(M, Y, ld, ns, dt, theta_host, res_host, nullptr, s);
+        return;
+    }
+    if (harmonic) {
+        // Y <- Y2 = Y1 conj(Mt)
+        tall_gemm(ns, Mt.as<double>(), T.as<double>(), Y);
+        T.reset();
+        harmonic_extract(M, Y, ld, ns, cplx, tau, h, tall_gram, tall_gemm, theta_host, res_host,
+                         s);
+        if (refill_counter) *refill_counter = counter;
         return;
     }
     // ---- Rayleigh-Ritz in the basis Y2 = Y1 T2

@@ -383,6 +383,7 @@ void solve_batched_impl(chebfd_ensemble* E, const chebfd_matrix* const* Hs, cons
     const bool cplx = E->m.complex_values;
     const chebfd_dtype d64 = cplx ? CHEBFD_C128 : CHEBFD_R64;
     const chebfd_dtype d32 = cplx ? CHEBFD_C64 : CHEBFD_R32;
+    CHEBFD_REQUIRE(p.flags == 0, CHEBFD_EUNSUPPORTED, "batched solve takes no solve flags");
     CHEBFD_REQUIRE(p.precision == CHEBFD_PRECISION_FP64 || p.precision == CHEBFD_PRECISION_MIXED,
                    CHEBFD_EUNSUPPORTED, "batched solve runs FP64 or MIXED precision");
     const bool mixed = p.precision == CHEBFD_PRECISION_MIXED;

@@ -13,7 +13,9 @@ void filter_block_df_impl(const Matrix& M, double alpha, double beta, const doub
                           void* X, int64_t ld, int nb, cudaStream_t s);
 void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype dt, uint64_t seed,
                    int64_t* refill_counter, double* theta_host, double* res_host, bool df,
-                   cudaStream_t s);
+                   bool harmonic, double tau, cudaStream_t s);
+void harmonic_ritz_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype dt, double tau,
+                        double* theta_host, double* res_host, cudaStream_t s);
 
 void filter_block_impl(const Matrix& M, double alpha, double beta, const double* gc, int Np,
                        void* X, int64_t ld, int nb, chebfd_dtype dt, double* moments,
@@ -97,6 +99,9 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
     CHEBFD_REQUIRE(p.precision >= CHEBFD_PRECISION_FP64 &&
                        p.precision <= CHEBFD_PRECISION_MIXED_DF,
                    CHEBFD_EINVAL, "unknown precision");
+    CHEBFD_REQUIRE((p.flags & ~CHEBFD_SOLVE_HARMONIC) == 0, CHEBFD_EINVAL, "unknown solve flags");
+    const bool harmonic = (p.flags & CHEBFD_SOLVE_HARMONIC) != 0;
+    const double tau = 0.5 * (p.lam_lo + p.lam_hi);
     const bool df = p.precision == CHEBFD_PRECISION_MIXED_DF;
     const bool mixed = p.precision == CHEBFD_PRECISION_MIXED || df;
     CHEBFD_REQUIRE(!mixed || M.val32 != nullptr, CHEBFD_EINVAL,
@@ -144,7 +149,8 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
         double t1 = now();
         t_filter += t1 - t0;
         // ---- steps 6-7: orthonormalise, Rayleigh-Ritz
-        ortho_rr_impl(M, Y64.p, ld, ns, d64, p.seed, &refill, theta.data(), res.data(), df, s);
+        ortho_rr_impl(M, Y64.p, ld, ns, d64, p.seed, &refill, theta.data(), res.data(), df,
+                      harmonic, tau, s);
         t_dense += now() - t1;
         // ---- step 8: window membership, ghosts, convergence
         acc_idx.clear();
@@ -265,6 +271,15 @@ chebfd_status chebfd_rayleigh_ritz(const chebfd_matrix* H, void* Y, int64_t ld, 
     return guarded([&] {
         CHEBFD_REQUIRE(H, CHEBFD_EINVAL, "null matrix");
         rayleigh_ritz_impl(H->m, Y, ld, ns, vdt, theta, res, HV, as_stream(stream));
+    });
+}
+
+chebfd_status chebfd_harmonic_ritz(const chebfd_matrix* H, void* Y, int64_t ld, int ns,
+                                   chebfd_dtype vdt, double tau, double* theta, double* res,
+                                   void* stream) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(H, CHEBFD_EINVAL, "null matrix");
+        harmonic_ritz_impl(H->m, Y, ld, ns, vdt, tau, theta, res, as_stream(stream));
     });
 }
 

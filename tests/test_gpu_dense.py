@@ -74,6 +74,53 @@ def test_rayleigh_ritz_exact_invariant_subspace():
     assert res.max() <= 1e-12
 
 
+@pytest.mark.parametrize("kind", ["topi", "graphene"])
+def test_harmonic_ritz_matches_oracle(kind):
+    """Harmonic Ritz extraction (Sec. 6) on a random orthonormal block: the
+    Rayleigh quotients of the oracle's harmonic vectors, unit vectors whose
+    residuals recomputed on the CPU equal the returned ones."""
+    if kind == "topi":
+        H = pkg.chebfd_matrix_create_lattice("topi", 4, 5, 6, W=1.1, seed=4)
+        Ho = lattice.to_scipy(*lattice.topi_csr(4, 5, 6, W=1.1, seed=4))
+        tau = 0.1
+    else:
+        H = pkg.chebfd_matrix_create_lattice("graphene", 30, 20, W=1.0, seed=4)
+        Ho = lattice.to_scipy(*lattice.graphene_csr(30, 20, W=1.0, seed=4))
+        tau = -0.05
+    Y0, _, _ = osvqb.svqb(workloads.random_block(1, H.n, 32, H.is_complex))
+    Y = torch.from_numpy(np.ascontiguousarray(Y0)).to(DEV)
+    theta, res = pkg.chebfd_harmonic_ritz(H, Y, tau)
+    rho_o, V_o, res_o, _ = orr.harmonic_ritz(Ho, Y0, tau)
+    normH = abs(Ho).sum(axis=1).max()
+    assert np.all(np.diff(theta) >= 0)
+    assert np.abs(theta - rho_o).max() <= 1e-10 * normH
+    assert np.abs(res - res_o).max() <= 1e-10 * normH
+    V = Y.cpu().numpy()
+    assert np.abs(np.linalg.norm(V, axis=0) - 1.0).max() <= 1e-12
+    assert np.allclose(orr.residual_norms(Ho, V, theta), res, atol=1e-11 * normH)
+
+
+def test_harmonic_ritz_exact_subspace_and_singular_fallback():
+    """On eigenvectors the harmonic pairs are exact; with tau equal to one of
+    their eigenvalues (Z^H Z singular) the ordinary Ritz pairs come back."""
+    H = pkg.chebfd_matrix_create_lattice("topi", 3, 3, 3, W=0.8, seed=9)
+    Ho = lattice.to_scipy(*lattice.topi_csr(3, 3, 3, W=0.8, seed=9))
+    lam, Vd = np.linalg.eigh(Ho.toarray())
+    Y = torch.from_numpy(np.ascontiguousarray(Vd[:, 40:52])).to(DEV)
+    theta, res = pkg.chebfd_harmonic_ritz(H, Y, 0.5 * (lam[40] + lam[51]) + 1e-3)
+    assert np.abs(theta - lam[40:52]).max() <= 1e-11
+    assert res.max() <= 1e-11
+    n = 64
+    d = np.arange(n) / 8.0 - 3.0                       # exact binary eigenvalues
+    D = pkg.chebfd_matrix_create_csr(np.arange(n + 1), np.arange(n), d)
+    E = np.zeros((n, 8))
+    E[np.arange(8) * 5, np.arange(8)] = 1.0            # unit vectors of eigenvalues d[5 k]
+    Ye = torch.from_numpy(E).to(DEV)
+    theta, res = pkg.chebfd_harmonic_ritz(D, Ye, d[15])
+    assert np.array_equal(theta, np.sort(d[np.arange(8) * 5]))
+    assert res.max() == 0.0
+
+
 def test_convert_block_round_trip():
     X0 = workloads.random_block(2, 1000, 16, True)
     X = torch.from_numpy(X0).to(DEV)
@@ -127,6 +174,33 @@ def test_solve_graphene_real_against_dense(precision):
     assert r["converged"] and r["nev"] == len(ew) > 0
     assert np.abs(np.sort(r["lam"]) - ew).max() <= 1e-10 * normH
     assert r["res"].max() <= 1e-9 * normH
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_df"])
+def test_solve_harmonic_smallest_insulator_against_dense(precision):
+    """Step 7 with harmonic Ritz pairs for the window centre: the same window
+    eigenvalues as dense diagonalisation and as the oracle's harmonic run,
+    residuals <= 1e-9 ||H||, unit vectors, in no more iterations than with
+    ordinary Ritz pairs."""
+    H = pkg.chebfd_matrix_create_lattice("topi", 8, 8, 8, t=1.0, m=1.0, W=0.5, seed=0,
+                                         also_single=True)
+    Ho = lattice.to_scipy(*lattice.topi_csr(8, 8, 8, t=1.0, m=1.0, W=0.5, seed=0))
+    r = pkg.chebfd_solve(H, -0.1, 0.1, 64, 200, eps=1e-9, kernel="jackson", precision=precision,
+                         extraction="harmonic")
+    ritz = pkg.chebfd_solve(H, -0.1, 0.1, 64, 200, eps=1e-9, kernel="jackson",
+                            precision=precision)
+    ew, _ = _dense_window(Ho, -0.1, 0.1)
+    normH = max(abs(r["a"]), abs(r["b"]))
+    assert r["converged"] and r["nev"] == len(ew) > 0
+    assert np.abs(np.sort(r["lam"]) - ew).max() <= 1e-10 * normH
+    assert r["res"].max() <= 1e-9 * normH
+    V = r["V"].cpu().numpy()
+    assert np.abs(np.linalg.norm(V, axis=0) - 1.0).max() <= 1e-12
+    assert np.abs(orr.residual_norms(Ho, V, r["lam"])).max() <= 1e-9 * normH
+    assert r["iterations"] <= ritz["iterations"]
+    ro = osolve.chebfd(Ho, r["a"], r["b"], -0.1, 0.1, 64, 200, 1e-9, kind="jackson", seed=0,
+                       extraction="harmonic")
+    assert np.abs(np.sort(ro["theta"]) - np.sort(r["lam"])).max() <= 1e-10 * normH
 
 
 def test_solve_reports_no_convergence():
