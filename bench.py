@@ -306,17 +306,20 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chir
     FP64 or double-float sweeps; FP64 Gram, Rayleigh-Ritz and residuals
     throughout), and the mixed double-float form with the MLP's parameters,
     with `matrix_free` once more with H's entries rebuilt in registers in
-    both the single-precision and the double-float steps, and that once more
-    with harmonic Ritz pairs for the window centre (Sec. 6)."""
+    both the single-precision and the double-float steps, that once more
+    with harmonic Ritz pairs for the window centre (Sec. 6), and that with
+    the filter window narrowed by half its half-width at half the degree."""
     import torch
     out = {}
     lams = {}
 
-    def run(name, ns_r, Np_r, kern, prec, extra=None, t_pre=0.0, extraction="ritz"):
+    def run(name, ns_r, Np_r, kern, prec, extra=None, t_pre=0.0, extraction="ritz",
+            window_inset=0.0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = pkg.chebfd_solve(H, -delta, delta, ns_r, Np_r, eps=eps, kernel=kern, precision=prec,
-                             a=a, b=b, max_iter=40, seed=0, extraction=extraction)
+                             a=a, b=b, max_iter=40, seed=0, extraction=extraction,
+                             window_inset=window_inset)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0 + t_pre
         normH = max(abs(r["a"]), abs(r["b"]))
@@ -366,6 +369,14 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chir
                         extra=extra, t_pre=t_choose, extraction="harmonic")
                 except pkg.ChebFDError as e:     # reported; the other forms stand
                     out["mixed_df_mlp_matrix_free_harmonic"] = {"error": str(e)}
+                # the window narrowed by half its half-width, half the degree
+                Np_i = max(8, int(round(0.5 * Np_m)))
+                try:
+                    run("mixed_df_mlp_matrix_free_harmonic_inset", ns_m, Np_i, kern_m,
+                        "mixed_df", extra=dict(extra, Np=Np_i, window_inset=0.5),
+                        t_pre=t_choose, extraction="harmonic", window_inset=0.5)
+                except pkg.ChebFDError as e:
+                    out["mixed_df_mlp_matrix_free_harmonic_inset"] = {"error": str(e)}
             finally:
                 H.set_matrix_free(False)
     out["eps"] = eps

@@ -24,11 +24,13 @@ def _poly_on_grid(gc, M):
 
 
 def damping_sigma(Np, delta, delta_p, c=0.0, a=-1.0, b=1.0, kind="lanczos", mu=2.0,
-                  per_period=64):
+                  per_period=64, inset=0.0):
     """sigma for I_T = [c-delta, c+delta], I_S = [c-delta-delta', c+delta+delta'];
-    p sampled at ``per_period`` points per theta period 2 pi / N_p."""
+    p sampled at ``per_period`` points per theta period 2 pi / N_p.  The window
+    of p is I_T narrowed by ``inset`` of its half-width (0: I_T itself)."""
     lo, hi = c - delta, c + delta
-    gc = coeffs.filter_coeffs(a, b, lo, hi, Np, kind, mu)
+    w = (1.0 - inset) * delta
+    gc = coeffs.filter_coeffs(a, b, c - w, c + w, Np, kind, mu)
     alpha, beta = coeffs.scaling(a, b)
     M = max(per_period * Np // 2, 4096)
     pg = _poly_on_grid(gc, M)

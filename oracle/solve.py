@@ -16,6 +16,10 @@ Readings of the paper taken here (the paper leaves them open):
   factor per iteration, so it would have been accepted;
 * restart (step 8b): the next search block is the full set of Ritz vectors,
   which spans the same space as the orthonormalised filtered block;
+* window_inset=f filters with the window W = 1 on [c - (1-f) d, c + (1-f) d]
+  inside the target interval [c - d, c + d] (Sec. 2.2 notes that windows with
+  W != 1 on part of I_T can converge faster); the window test and the
+  convergence test still use the target interval;
 * extraction="harmonic" replaces step 7's Ritz pairs by harmonic Ritz pairs
   for the target tau = (lam_lo + lam_hi) / 2 (rr.harmonic_ritz): window
   membership, ghosts and convergence then use their Rayleigh quotients and
@@ -38,7 +42,8 @@ def search_vectors(seed, D, ns, complex_values):
 
 
 def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
-           max_iter=40, filter_fn=None, X0=None, complex_values=None, extraction="ritz"):
+           max_iter=40, filter_fn=None, X0=None, complex_values=None, extraction="ritz",
+           window_inset=0.0):
     """Run ChebFD; returns a dict with the accepted pairs and the iteration log.
 
     ``filter_fn(X)``, when given, replaces the recurrence of Fig. ChebFD by
@@ -47,7 +52,10 @@ def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
     if complex_values is None:
         complex_values = np.iscomplexobj(H.data) if hasattr(H, "data") else False
     alpha, beta = coeffs.scaling(a, b)
-    gc = coeffs.filter_coeffs(a, b, lam_lo, lam_hi, Np, kind, mu)
+    if not 0.0 <= window_inset < 1.0:
+        raise ValueError("need 0 <= window_inset < 1")
+    c, d = 0.5 * (lam_lo + lam_hi), 0.5 * (lam_hi - lam_lo) * (1.0 - window_inset)
+    gc = coeffs.filter_coeffs(a, b, c - d, c + d, Np, kind, mu)
     normH = max(abs(a), abs(b))
     X = search_vectors(seed, D, ns, complex_values) if X0 is None else np.array(X0, copy=True)
     refill = 0

@@ -143,7 +143,7 @@ class Params(ctypes.Structure):
                 ("ns", ctypes.c_int32), ("Np", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("nb", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("lanczos_steps", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("window_inset", ctypes.c_double)]
 
 
 class ResultInfo(ctypes.Structure):
@@ -420,14 +420,16 @@ EXTRACTION = {"ritz": 0, "harmonic": 1}
 
 def chebfd_solve(H, lam_lo, lam_hi, ns, Np, eps=1e-9, kernel="lanczos", mu=2.0, nb=0,
                  precision="fp64", max_iter=50, seed=0, a=0.0, b=0.0, lanczos_steps=30,
-                 stream=None, extraction="ritz"):
+                 stream=None, extraction="ritz", window_inset=0.0):
     """Run ChebFD; returns a dict with lambda, res (numpy), V (torch, device) and the log.
-    extraction="harmonic" uses harmonic Ritz pairs for the window centre."""
+    extraction="harmonic" uses harmonic Ritz pairs for the window centre;
+    window_inset=f filters with the window narrowed by f of the half-width."""
     import torch
     p = Params(lam_lo=lam_lo, lam_hi=lam_hi, eps=eps, a=a, b=b, mu=mu, ns=ns, Np=Np,
                kernel=KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel), nb=nb,
                precision=PRECISION[precision], max_iter=max_iter,
-               lanczos_steps=lanczos_steps, flags=EXTRACTION[extraction], seed=seed)
+               lanczos_steps=lanczos_steps, flags=EXTRACTION[extraction], seed=seed,
+               window_inset=window_inset)
     h = c_vp()
     st = lib().chebfd_solve(H.handle, ctypes.byref(p), _stream(stream), ctypes.byref(h))
     if st not in (0, 5) or not h:
@@ -546,7 +548,7 @@ def _result_dict(h, n, is_complex, st=0, vectors=True):
 
 def chebfd_solve_batched(E, matrices, a, b, lam_lo, lam_hi, ns, Np, eps=1e-9, kernel="lanczos",
                          mu=2.0, precision="fp64", max_iter=50, seed=0, vectors=False,
-                         stream=None):
+                         stream=None, window_inset=0.0):
     """ChebFD on every ensemble member; returns (list of per-member dicts, iterations)."""
     cnt = len(matrices)
     arr = (c_vp * cnt)(*[m.handle for m in matrices])
@@ -555,7 +557,7 @@ def chebfd_solve_batched(E, matrices, a, b, lam_lo, lam_hi, ns, Np, eps=1e-9, ke
     p = Params(lam_lo=lam_lo, lam_hi=lam_hi, eps=eps, a=0.0, b=0.0, mu=mu, ns=ns, Np=Np,
                kernel=KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel), nb=0,
                precision=PRECISION[precision], max_iter=max_iter, lanczos_steps=0,
-               flags=0, seed=seed)
+               flags=0, seed=seed, window_inset=window_inset)
     outs = (c_vp * cnt)()
     its = ctypes.c_int32()
     _check(lib().chebfd_solve_batched(E.handle, arr, a.ctypes.data_as(c_dp),

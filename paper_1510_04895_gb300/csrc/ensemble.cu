@@ -395,12 +395,16 @@ void solve_batched_impl(chebfd_ensemble* E, const chebfd_matrix* const* Hs, cons
         CHEBFD_REQUIRE(bv[i] > av[i], CHEBFD_EINVAL, "need b > a for every member");
         outs[i] = nullptr;
     }
-    // per-member coefficients of the common window
+    // per-member coefficients of the common window (narrowed by window_inset)
+    CHEBFD_REQUIRE(p.window_inset >= 0.0 && p.window_inset < 1.0, CHEBFD_EINVAL,
+                   "need 0 <= window_inset < 1");
+    const double wc = 0.5 * (p.lam_lo + p.lam_hi),
+                 wh = 0.5 * (p.lam_hi - p.lam_lo) * (1.0 - p.window_inset);
     std::vector<double> al(count), be(count), gc((size_t)count * (p.Np + 1));
     for (int i = 0; i < count; ++i) {
         al[i] = 2.0 / (bv[i] - av[i]);
         be[i] = (av[i] + bv[i]) / (av[i] - bv[i]);
-        const chebfd_status st = chebfd_window_coeffs(av[i], bv[i], p.lam_lo, p.lam_hi, p.Np,
+        const chebfd_status st = chebfd_window_coeffs(av[i], bv[i], wc - wh, wc + wh, p.Np,
                                                       (chebfd_kernel)p.kernel, p.mu,
                                                       gc.data() + (size_t)i * (p.Np + 1));
         CHEBFD_REQUIRE(st == CHEBFD_OK, st, "coefficient construction failed");

@@ -90,6 +90,8 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
     CHEBFD_REQUIRE(p.Np >= 2, CHEBFD_EINVAL, "need Np >= 2");
     CHEBFD_REQUIRE(p.lam_hi > p.lam_lo, CHEBFD_EINVAL, "need lam_hi > lam_lo");
     CHEBFD_REQUIRE(p.eps > 0.0, CHEBFD_EINVAL, "need eps > 0");
+    CHEBFD_REQUIRE(p.window_inset >= 0.0 && p.window_inset < 1.0, CHEBFD_EINVAL,
+                   "need 0 <= window_inset < 1");
     if (p.mu <= 0.0) p.mu = 2.0;
     if (p.max_iter <= 0) p.max_iter = 50;
     if (p.lanczos_steps <= 0) p.lanczos_steps = 30;
@@ -112,7 +114,10 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
     if (!(b > a)) scale_bounds_impl(M, p.lanczos_steps, p.seed, &a, &b, s);
     const double normH = std::max(std::fabs(a), std::fabs(b));
     const double alpha = 2.0 / (b - a), beta = (a + b) / (a - b);
-    const std::vector<double> gc = coefficients(a, b, p.lam_lo, p.lam_hi, p.Np, p.kernel, p.mu);
+    // filter window: the target interval, narrowed by window_inset of its half-width
+    const double wc = 0.5 * (p.lam_lo + p.lam_hi),
+                 wh = 0.5 * (p.lam_hi - p.lam_lo) * (1.0 - p.window_inset);
+    const std::vector<double> gc = coefficients(a, b, wc - wh, wc + wh, p.Np, p.kernel, p.mu);
     const int64_t n = M.n;
     const int ns = p.ns;
     const int64_t ld = ns;  // rows start on 16 bytes in every precision (ns % 4 == 0)

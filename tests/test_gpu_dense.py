@@ -203,6 +203,27 @@ def test_solve_harmonic_smallest_insulator_against_dense(precision):
     assert np.abs(np.sort(ro["theta"]) - np.sort(r["lam"])).max() <= 1e-10 * normH
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed_df"])
+def test_solve_inset_window_half_degree_against_dense(precision):
+    """The filter window narrowed by half the target half-width with half
+    the degree (N_p = 100, Lanczos): all window eigenvalues of the dense
+    eigensolver, residuals <= 1e-9 ||H||, the oracle's eigenvalues."""
+    H = pkg.chebfd_matrix_create_lattice("topi", 8, 8, 8, t=1.0, m=1.0, W=0.5, seed=0,
+                                         also_single=True)
+    Ho = lattice.to_scipy(*lattice.topi_csr(8, 8, 8, t=1.0, m=1.0, W=0.5, seed=0))
+    r = pkg.chebfd_solve(H, -0.1, 0.1, 64, 100, eps=1e-9, kernel="lanczos", precision=precision,
+                         window_inset=0.5)
+    ew, _ = _dense_window(Ho, -0.1, 0.1)
+    normH = max(abs(r["a"]), abs(r["b"]))
+    assert r["converged"] and r["nev"] == len(ew) > 0
+    assert np.abs(np.sort(r["lam"]) - ew).max() <= 1e-10 * normH
+    assert r["res"].max() <= 1e-9 * normH
+    ro = osolve.chebfd(Ho, r["a"], r["b"], -0.1, 0.1, 64, 100, 1e-9, seed=0, window_inset=0.5)
+    assert np.abs(np.sort(ro["theta"]) - np.sort(r["lam"])).max() <= 1e-10 * normH
+    with pytest.raises(pkg.ChebFDError):
+        pkg.chebfd_solve(H, -0.1, 0.1, 64, 100, window_inset=1.0)
+
+
 def test_solve_reports_no_convergence():
     H = pkg.chebfd_matrix_create_lattice("topi", 4, 4, 4, W=0.5, seed=0)
     r = pkg.chebfd_solve(H, -0.2, 0.2, 16, 20, eps=1e-12, kernel="jackson", max_iter=1)

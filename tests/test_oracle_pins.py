@@ -505,6 +505,34 @@ def test_chebfd_harmonic_extraction_small_topi_against_dense():
     assert r["iterations"] <= ritz["iterations"]
 
 
+def test_chebfd_inset_window_halves_the_degree_small_topi():
+    """A window narrowed by half the target half-width (W = 1 on [-0.05, 0.05]
+    inside I_T = [-0.1, 0.1], Sec. 2.2) with half the degree (N_p = 100,
+    Lanczos): all window eigenvalues of the dense eigensolver in as many
+    iterations as the rectangular window at N_p = 200, half the spMVMs; the
+    rectangular window at N_p = 100 needs more iterations."""
+    H = lattice.to_scipy(*lattice.topi_csr(8, 8, 8, t=1.0, m=1.0, W=0.5, seed=0))
+    a, b = bounds.lanczos_bounds(H, 30, seed=0)
+    e = np.linalg.eigvalsh(H.toarray())
+    ew = e[np.abs(e) <= 0.1]
+    r = solve.chebfd(H, a, b, -0.1, 0.1, 64, 100, 1e-9, seed=0, window_inset=0.5)
+    assert r["converged"] and len(r["theta"]) == len(ew)
+    assert np.abs(np.sort(r["theta"]) - ew).max() <= 1e-10 * r["normH"]
+    rect = solve.chebfd(H, a, b, -0.1, 0.1, 64, 200, 1e-9, seed=0)
+    assert r["iterations"] <= rect["iterations"]
+
+
+def test_inset_window_lowers_eta():
+    """Sec. 2.3 quality measure at delta = delta' = 1e-2 on [-1, 1] (Lanczos
+    mu = 2): the rectangular window reproduces Tab. lanczoskernel's centre
+    value eta_0 = 2.58 / delta'; the window narrowed by half the half-width
+    reaches eta <= 0.8 of it with N_p^opt <= 0.7 of the rectangular one."""
+    n_r, e_r = quality.optimal_Np(1e-2, 1e-2, n_lo=400, n_hi=900)
+    n_i, e_i = quality.optimal_Np(1e-2, 1e-2, n_lo=250, n_hi=700, inset=0.5)
+    assert abs(e_r - 258.0) <= 0.02 * 258.0
+    assert e_i <= 0.8 * e_r and n_i <= 0.7 * n_r
+
+
 def test_mlp_gradient_matches_central_differences():
     from oracle import mlp
     rs = np.random.default_rng(0)
