@@ -12,6 +12,11 @@ paper finds N_T = 144 after a KPM estimate of 124), residuals and seconds.
 
     python -m paper_1510_04895_gb300.repro_topi [--precision mixed_df]
         [--kernels jackson lanczos1 lanczos2 lanczos3] [--L 256 256 10] [--seed 0]
+        [--harmonic] [--inset F --Np-scale S]
+
+--harmonic takes harmonic Ritz pairs for the window centre (Sec. 6);
+--inset F filters with the window narrowed by F of its half-width (Sec. 2.2),
+usually with --Np-scale 0.5 (N_p scaled by S).
 
 The disorder realisation is this project's (SplitMix64 stream 0, seed 0);
 the paper's is not published, so N_T and N_MVM agree only statistically.
@@ -41,6 +46,9 @@ def main(argv=None):
     p.add_argument("--precision", default="mixed_df", choices=["fp64", "mixed", "mixed_df"])
     p.add_argument("--kernels", nargs="+", default=list(KERNELS), choices=list(KERNELS))
     p.add_argument("--max-iter", dest="max_iter", type=int, default=30)
+    p.add_argument("--harmonic", action="store_true")
+    p.add_argument("--inset", type=float, default=0.0)
+    p.add_argument("--Np-scale", dest="np_scale", type=float, default=1.0)
     args = p.parse_args(argv)
 
     import numpy as np
@@ -64,16 +72,19 @@ def main(argv=None):
         kern, mu = KERNELS[name]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = pkg.chebfd_solve(H, lo, hi, args.ns, args.Np, eps=args.eps_abs / norm, kernel=kern,
+        Np = max(8, int(round(args.Np * args.np_scale)))
+        r = pkg.chebfd_solve(H, lo, hi, args.ns, Np, eps=args.eps_abs / norm, kernel=kern,
                              mu=mu, precision=args.precision, a=a, b=b, max_iter=args.max_iter,
-                             seed=0)
+                             seed=0, extraction="harmonic" if args.harmonic else "ritz",
+                             window_inset=args.inset)
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
         lam = np.sort(r["lam"])
         print(json.dumps({
             "kernel": name, "precision": args.precision, "converged": r["converged"],
+            "Np": Np, "harmonic": args.harmonic, "window_inset": args.inset,
             "iterations": r["iterations"], "fp64_filter_iterations": r["fp64_iterations"],
-            "n_mvm": r["iterations"] * args.ns * args.Np, "n_target_found": r["nev"],
+            "n_mvm": r["iterations"] * args.ns * Np, "n_target_found": r["nev"],
             "max_residual": float(r["res"].max()) if r["nev"] else None,
             "lambda_range": [float(lam[0]), float(lam[-1])] if r["nev"] else None,
             "seconds": sec, "seconds_filter": r["seconds_filter"],

@@ -288,6 +288,9 @@ MUTANTS = {
     "KPM count without the factor D": (
         _wrap(kpm, "count_in_window", lambda o: lambda mu, D, *a, **k: o(mu, 1, *a, **k)),
         [pins.test_kpm_trace_exact_on_diagonal_and_count]),
+    "inset window widened instead of narrowed": (
+        _wrap(quality, "damping_sigma", lambda o: lambda *a, inset=0.0, **k: o(*a, inset=-inset, **k)),
+        [pins.test_inset_window_lowers_eta]),
     "eta with the natural logarithm": (
         _wrap(quality, "eta", _eta_natural_log),
         [pins.test_tab_lanczoskernel_scaling_constants]),
