@@ -1,7 +1,8 @@
-// Matrix-free complex64 Chebyshev step (MODE_STEP) for the insulator
-// lattices: w = 2 (alpha H + beta) u - w ; y += c w with H's entries rebuilt
-// in registers from the lattice description instead of read from memory
-// (the paper's on-the-fly matrices, Sec. 1).
+// Matrix-free Chebyshev steps (MODE_STEP) for the insulator lattices, in
+// complex64 and in double-float arithmetic: w = 2 (alpha H + beta) u - w ;
+// y += c w with H's entries rebuilt in registers from the lattice
+// description instead of read from memory (the paper's on-the-fly matrices,
+// Sec. 1).
 //
 // Same mapping as the blocked step (step_bell.cu): one group of G lanes per
 // site computes its 4 orbital rows, each lane one 16-byte chunk (two complex
