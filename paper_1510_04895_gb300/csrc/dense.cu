@@ -52,8 +52,11 @@ struct Handles {
     cusolverDnHandle_t solver = nullptr;
 };
 
+// One cuBLAS / cuSOLVER handle pair per host thread and device: a handle is
+// bound to one stream at a time, so threads never share one.  The handles
+// live until the process exits.
 Handles& handles_for_current_device(cudaStream_t s) {
-    static std::map<int, Handles> cache;
+    thread_local std::map<int, Handles> cache;
     int dev = 0;
     CHEBFD_CHECK_CUDA(cudaGetDevice(&dev));
     Handles& h = cache[dev];
