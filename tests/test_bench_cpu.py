@@ -1,5 +1,6 @@
 """Host logic of bench.py (no GPU): workload parameters from the frozen
-windows, the traffic reader's source-hash check and the peak lookup."""
+windows, the traffic reader's source-hash check, the peak lookup and the
+sequence of solve forms (against a stand-in for the library)."""
 import os
 
 import pytest
@@ -49,3 +50,70 @@ def test_peaks_fall_back_without_the_measured_file(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     peaks, kind = bench.measured_peaks()
     assert kind == "fallback" and peaks["hbm_gbs"] == 6800.0
+
+
+class _FakeLib:
+    """Stands in for the library in bench_solve: records the solve calls and
+    fails the one form a test names."""
+
+    class ChebFDError(Exception):
+        pass
+
+    def __init__(self, fail=None):
+        self.calls, self.fail = [], fail
+
+    def chebfd_solve(self, H, lo, hi, ns, Np, eps, kernel, precision, a, b, max_iter, seed,
+                     extraction="ritz", window_inset=0.0):
+        import numpy as np
+        key = (precision, extraction, window_inset)
+        self.calls.append(dict(ns=ns, Np=Np, kernel=kernel, precision=precision,
+                               extraction=extraction, window_inset=window_inset))
+        if self.fail == key:
+            raise self.ChebFDError("planted failure")
+        lam = np.array([-0.1, -0.05, 0.05, 0.1])
+        return dict(a=a, b=b, lam=lam, res=np.full(4, 1e-10), nev=4, iterations=5,
+                    fp64_iterations=1, converged=True, seconds_filter=1.0, seconds_dense=0.5,
+                    n_mvm=5 * ns * Np)
+
+    def set_matrix_free(self, on):
+        self.calls.append(dict(matrix_free=on))
+
+    class MLP:
+        def __init__(self, n_in, n_h):
+            pass
+
+        def set_params(self, p):
+            pass
+
+    def chebfd_choose_params(self, H, lo, hi, mlp, a, b, m_feat):
+        return 192, 610, "lanczos", 94.0
+
+
+@pytest.mark.parametrize("fail", [None, ("mixed_df", "harmonic", 0.5),
+                                  ("mixed_df", "harmonic", 0.0)])
+def test_solve_forms_of_the_benchmark(monkeypatch, fail):
+    """bench_solve runs every form with the parameters it reports (the inset
+    form at half the MLP's degree), restores the matrix-free switch, and a
+    failing harmonic form is reported without losing the others."""
+    import torch
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
+    fake = _FakeLib(fail)
+    H = fake
+    out = bench.bench_solve(fake, H, -4.2, 4.2, 0.14, 309, 256, "fake", precisions=("fp64",),
+                            matrix_free=True)
+    forms = ("fp64", "mixed_df_mlp", "mixed_df_mlp_matrix_free",
+             "mixed_df_mlp_matrix_free_harmonic", "mixed_df_mlp_matrix_free_harmonic_inset")
+    for f in forms:
+        assert f in out
+    solves = [c for c in fake.calls if "Np" in c]
+    assert [c["extraction"] for c in solves] == ["ritz", "ritz", "ritz", "harmonic", "harmonic"]
+    assert solves[-1]["window_inset"] == 0.5 and solves[-1]["Np"] == 305
+    assert fake.calls[-1] == dict(matrix_free=False)
+    if fail is None:
+        assert out["mixed_df_mlp_matrix_free_harmonic_inset"]["Np"] == 305
+        assert out["speedup_mixed_df_mlp_matrix_free_harmonic_inset_over_fp64"] > 0
+    else:
+        name = ("mixed_df_mlp_matrix_free_harmonic_inset" if fail[2] else
+                "mixed_df_mlp_matrix_free_harmonic")
+        assert out[name] == {"error": "planted failure"}
+        assert out["mixed_df_mlp_matrix_free"]["converged"]
