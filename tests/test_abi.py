@@ -62,3 +62,42 @@ def test_invalid_arguments_are_reported(built):
     assert e.value.status == 1 and "b > a" in str(e.value)
     with pytest.raises(built.ChebFDError):
         built.chebfd_window_coeffs(-1.0, 1.0, -0.1, 0.1, 10, kernel=17)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "chebfd.h"
+
+int main(void) {
+    double gc[41];
+    chebfd_status st;
+    int k;
+    if (chebfd_abi_version() != CHEBFD_ABI_VERSION) return 2;
+    st = chebfd_window_coeffs(-2.0, 3.0, -0.3, 0.4, 40, CHEBFD_KERNEL_JACKSON, 2.0, gc);
+    if (st != CHEBFD_OK) return 3;
+    for (k = 0; k <= 40; ++k) printf("%.17g\n", gc[k]);
+    st = chebfd_window_coeffs(1.0, -1.0, -0.1, 0.1, 10, CHEBFD_KERNEL_LANCZOS, 2.0, gc);
+    printf("%d %s | %s\n", (int)st, chebfd_status_string(st), chebfd_last_error());
+    return 0;
+}
+"""
+
+
+def test_header_compiles_as_c99_and_links(built, tmp_path):
+    """A plain C99 program (-Wall -Werror -pedantic) includes chebfd.h, links
+    libchebfd.so and calls host-only entry points: the coefficients match the
+    oracle, an invalid call returns EINVAL with a message."""
+    from oracle import coeffs
+    src = tmp_path / "use_chebfd.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "use_chebfd"
+    libdir = os.path.dirname(built.LIB_PATH)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-lchebfd", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    lines = out.strip().splitlines()
+    got = np.array([float(x) for x in lines[:41]])
+    ref = coeffs.filter_coeffs(-2.0, 3.0, -0.3, 0.4, 40, "jackson")
+    assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max() * 10
+    assert lines[41].startswith("1 ") and "b > a" in lines[41]
