@@ -47,7 +47,7 @@ typedef enum chebfd_status {
     CHEBFD_ENUMERIC = 4,     /* NaN, or the recurrence diverged: spec(H) not inside [a,b] */
     CHEBFD_ENOCONV = 5,      /* iteration limit reached before convergence */
     CHEBFD_ETIMEOUT = 6,     /* a bounded device-side wait gave up */
-    CHEBFD_EUNSUPPORTED = 7  /* valid request this build does not implement */
+    CHEBFD_EUNSUPPORTED = 7  /* valid request the library does not implement */
 } chebfd_status;
 
 typedef enum chebfd_dtype {
@@ -361,7 +361,7 @@ chebfd_status chebfd_convert_block(const void* X, chebfd_dtype xdt, int64_t ldx,
                                    chebfd_dtype ydt, int64_t ldy, int64_t n, int nb,
                                    void* stream);
 
-/* --------------------------------------------- batched ensembles (the benchmark spec) */
+/* ---------------------------------------------------------- batched ensembles */
 
 /* Ensembles of independent matrices (e.g. disorder realisations of uneven
  * size) filtered together.  The paper filters one matrix; batching many is
@@ -446,7 +446,7 @@ chebfd_status chebfd_choose_params(const chebfd_matrix* H, double a, double b, d
                                    int* ns, int* Np, int* kernel, double* n_target,
                                    void* stream);
 
-/* --------------------------------------------------- MLP (K9, the benchmark spec) */
+/* ---------------------------------------------------------------- MLP (K9) */
 
 /* Fully connected network x (n_in) -> tanh (n_hidden) -> tanh (n_hidden) ->
  * 3 outputs (log N_p, log n_s, kernel logit), FP32 on the device, trained

@@ -1,5 +1,6 @@
-// Parameter-predicting MLP (north-star "learned parts"; the paper's nearest
-// passage is the adaptive choice of N_p and N_S from the DOS, Sec. 6):
+// Parameter-predicting MLP (a learned choice of the filter parameters; the
+// paper's nearest passage is the adaptive choice of N_p and N_S from the DOS,
+// Sec. 6):
 // features of (H, window) -> tanh(W1 x + b1) -> tanh(W2 h1 + b2) -> W3 h2 + b3
 // with outputs (log N_p, log n_s, kernel logit).  FP32 training and inference
 // on the GPU with the kernels below (forward, loss, backward, Adam); every sum
