@@ -13,7 +13,8 @@ values tau + 1/mu_k (equivalently: the Ritz values of (H - tau)^-1 on the
 subspace Z spans, inverted and shifted back).  Reading: the eigenvalue
 estimate of a harmonic vector v_k = Y s_k / ||Y s_k|| is its Rayleigh quotient
 rho_k = v_k^H H v_k, its residual ||H v_k - rho_k v_k||; pairs are ordered by
-ascending rho.
+ascending rho.  When Z^H Z is not positive definite (a basis vector is an
+exact eigenvector at tau) the ordinary Ritz pairs are returned instead.
 """
 import numpy as np
 import scipy.linalg
@@ -45,7 +46,11 @@ def harmonic_ritz(H, Y, tau):
     G = 0.5 * (G + G.conj().T)
     K = Z.conj().T @ Z
     K = 0.5 * (K + K.conj().T)
-    mu, S = scipy.linalg.eigh(G, K)
+    try:
+        mu, S = scipy.linalg.eigh(G, K)
+    except np.linalg.LinAlgError:
+        theta, V, res = rayleigh_ritz(H, Y)
+        return theta, V, res, theta.copy()
     S = S / np.linalg.norm(Y @ S, axis=0)[None, :]
     V = Y @ S
     HV = HY @ S

@@ -430,6 +430,18 @@ def test_harmonic_ritz_exact_on_invariant_subspace():
     assert np.allclose(np.linalg.norm(Vh, axis=0), 1.0)
 
 
+def test_harmonic_ritz_falls_back_to_ritz_pairs_when_singular():
+    """tau equal to the eigenvalue of a basis vector makes Z^H Z singular:
+    the ordinary Ritz pairs (here the exact eigenpairs) come back."""
+    d = np.arange(64) / 8.0 - 3.0
+    H = sp.diags(d).tocsr()
+    E = np.zeros((64, 8))
+    E[np.arange(8) * 5, np.arange(8)] = 1.0
+    rho, V, res, _ = rr.harmonic_ritz(H, E, d[15])
+    assert np.array_equal(rho, np.sort(d[np.arange(8) * 5]))
+    assert res.max() == 0.0
+
+
 def test_harmonic_values_are_inverse_ritz_values_of_the_shifted_inverse():
     """Harmonic Ritz values of H on span(Y) for target tau are tau + 1/mu with
     mu the Ritz values of (H - tau)^-1 on span((H - tau) Y) (Morgan 1991):
