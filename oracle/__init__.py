@@ -18,7 +18,7 @@ Modules
   filter        the filter recurrence of Fig. ChebFD and Chebyshev moments (Sec. 4)
   kpm           stochastic-trace KPM moments, DOS and target count (Sec. 3.1 step 1-2)
   bounds        Lanczos estimate of the spectral interval [a, b] (Sec. 3.1 step 1)
-  svqb          rank-revealing SVQB orthonormalisation with Kahan sums (Sec. 3.1 step 6)
+  svqb          rank-revealing SVQB orthonormalisation, plain FP64 Gram (Sec. 3.1 step 6)
   rr            Rayleigh-Ritz pairs and residual norms (Sec. 3.1 step 7)
   solve         the ChebFD outer iteration with ghost rejection (Sec. 3.1 steps 5-8)
   quality       damping factor sigma, quality eta, optimal N_p (Sec. 2.3, 2.4)

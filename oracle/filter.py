@@ -1,10 +1,12 @@
-"""Polynomial filter application, Fig. ChebFD (Sec. 3.1 step 5) - oracle side.
+"""Polynomial filter application (Sec. 2.1, Sec. 3.1 step 5) - oracle side.
 
-The block X (N x n_b) is replaced by p[H] X = sum_n gc[n] T_n(alpha H + beta) X
-through the three-term recurrence of Sec. 2.1, in exactly the step order of
-Fig. ChebFD: two start steps, then N_p - 2 steps that each apply
-A = alpha H + beta once and add gc[n] w to the accumulated block.  A u is
-evaluated as alpha (H u) + beta u, with H u a CSR product (ascending columns).
+The block X (N x n_b) is replaced by p[H] X = sum_{n=0}^{N_p} gc[n] T_n(A) X with
+A = alpha H + beta, the Chebyshev polynomials of A applied to X by their
+three-term recurrence T_0 = 1, T_1(A) = A, T_{n+1}(A) = 2 A T_n(A) - T_{n-1}(A).
+Each T_n(A) X costs one product with A and is added to the sum as soon as it
+exists (ascending n, the order the filter of Fig. ChebFD uses), so only the
+two latest vectors are kept.  A v is evaluated as alpha (H v) + beta v, with
+H v a CSR product (ascending columns).
 
 The Chebyshev moments of Sec. 4, mu_n[k] = <x_k, T_n(A) x_k>, are computed
 here literally from their definition (the original x_k kept aside), for
@@ -19,19 +21,17 @@ def apply_A(H, alpha, beta, v):
 
 
 def filter_block(H, alpha, beta, gc, X):
-    """Return p[H] X following Fig. ChebFD; H is a scipy CSR matrix."""
+    """Return sum_n gc[n] T_n(A) X (Sec. 2.1); H is a scipy CSR matrix, N_p >= 2."""
     Np = len(gc) - 1
     if Np < 2:
-        raise ValueError("Fig. ChebFD needs N_p >= 2")
-    x = np.array(X, copy=True)
-    u = apply_A(H, alpha, beta, x)                 # u = A x
-    w = 2.0 * apply_A(H, alpha, beta, u) - x       # w = 2 A u - x
-    x = gc[0] * x + gc[1] * u + gc[2] * w          # x = g0c0 x + g1c1 u + g2c2 w
-    for n in range(3, Np + 1):
-        u, w = w, u                                # swap(w, u)
-        w = 2.0 * apply_A(H, alpha, beta, u) - w   # w = 2 A u - w
-        x = x + gc[n] * w                          # x = x + gn cn w
-    return x
+        raise ValueError("the filter needs N_p >= 2")
+    t_prev = np.array(X, copy=True)                 # T_0(A) X
+    t_cur = apply_A(H, alpha, beta, t_prev)         # T_1(A) X
+    y = gc[0] * t_prev + gc[1] * t_cur
+    for n in range(2, Np + 1):
+        t_prev, t_cur = t_cur, 2.0 * apply_A(H, alpha, beta, t_cur) - t_prev   # T_n(A) X
+        y = y + gc[n] * t_cur
+    return y
 
 
 def chebyshev_vectors(H, alpha, beta, X, nmax):

@@ -11,9 +11,11 @@ Readings of the paper taken here (the paper leaves them open):
   accepted in-window pair below eps ||H||; the window is closed,
   lam_lo <= theta <= lam_hi.  Step 8a holds vacuously for a window without
   eigenvalues; such a window is taken as empty once two successive
-  iterations (from the second on, when ghosts are recognised) accept no
-  in-window pair - a true eigenpair's residual falls by the filter's damping
-  factor per iteration, so it would have been accepted;
+  iterations (from the second on) have no Ritz value in the window at all,
+  ghosts included.  Ghost-flagged pairs do not count as evidence of an empty
+  window: with a weak filter (damping worse than 10x per iteration) the true
+  pairs are ghost-flagged until their residuals fall below sqrt(eps) ||H||,
+  and the iteration has to go on (or end unconverged at max_iter);
 * restart (step 8b): the next search block is the full set of Ritz vectors,
   which spans the same space as the orthonormalised filtered block;
 * window_inset=f filters with the window W = 1 on [c - (1-f) d, c + (1-f) d]
@@ -80,7 +82,7 @@ def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
                     ghost[k] = True
         acc = inwin & ~ghost
         converged = bool(acc.any()) and bool(np.all(res[acc] <= eps * normH))
-        empty_now = prev is not None and not acc.any()
+        empty_now = prev is not None and not inwin.any()
         if empty_now and prev_empty:
             converged = True
         prev_empty = empty_now

@@ -33,18 +33,18 @@ def _wrap(module, name, fn):
 
 
 def _filter_block(step_factor=2.0, gc_shift=0, last=None):
-    """Fig. ChebFD with one planted change to the loop."""
+    """The Chebyshev filter sum with one planted change to the recurrence loop
+    (n >= 3): the factor 2, the coefficient index, or the last degree."""
     def f(H, alpha, beta, gc, X):
         Np = len(gc) - 1
-        x = np.array(X, copy=True)
-        u = filt.apply_A(H, alpha, beta, x)
-        w = 2.0 * filt.apply_A(H, alpha, beta, u) - x
-        x = gc[0] * x + gc[1] * u + gc[2] * w
-        for n in range(3, (Np if last is None else last) + 1):
-            u, w = w, u
-            w = step_factor * filt.apply_A(H, alpha, beta, u) - w
-            x = x + gc[n - gc_shift] * w
-        return x
+        t_prev = np.array(X, copy=True)
+        t_cur = filt.apply_A(H, alpha, beta, t_prev)
+        y = gc[0] * t_prev + gc[1] * t_cur
+        for n in range(2, (Np if last is None else last) + 1):
+            k = step_factor if n >= 3 else 2.0
+            t_prev, t_cur = t_cur, k * filt.apply_A(H, alpha, beta, t_cur) - t_prev
+            y = y + gc[n - (gc_shift if n >= 3 else 0)] * t_cur
+        return y
     return f
 
 
@@ -182,6 +182,66 @@ def _eta_natural_log(orig):
     return f
 
 
+def _sell_layout(row_major=False, pad_col_zero=False):
+    """sell_from_csr with a planted layout mistake, and a decoder that matches
+    it (so the round-trip pin alone cannot see it): slots row-major inside a
+    chunk (entry j of local row l at chunk_ptr + l*width + j), or padding
+    slots pointing at column 0 instead of their own row."""
+    def slot(S, k, l, j):
+        wdt = S["chunk_len"][k]
+        return S["chunk_ptr"][k] + (l * wdt + j if row_major else j * S["C"] + l)
+
+    def patch(mp):
+        orig = sell.sell_from_csr
+
+        def build(rowptr, col, val, C, sigma):
+            S = orig(rowptr, col, val, C, sigma)      # sort, widths, pointers kept
+            scol, sval = np.zeros_like(S["col"]), np.zeros_like(S["val"])
+            for k in range(S["nchunks"]):
+                for l in range(C):
+                    r = k * C + l
+                    if r >= S["n"]:
+                        continue
+                    o = S["perm"][r]
+                    b, e = rowptr[o], rowptr[o + 1]
+                    for j in range(S["chunk_len"][k]):
+                        pos = slot(S, k, l, j)
+                        if j < e - b:
+                            scol[pos], sval[pos] = col[b + j], val[b + j]
+                        else:
+                            scol[pos] = 0 if pad_col_zero else o
+            S["col"], S["val"] = scol, sval
+            return S
+
+        def decode(S):
+            rows = [[] for _ in range(S["n"])]
+            for k in range(S["nchunks"]):
+                for l in range(S["C"]):
+                    r = k * S["C"] + l
+                    if r < S["n"]:
+                        for j in range(S["chunk_len"][k]):
+                            pos = slot(S, k, l, j)
+                            rows[S["perm"][r]].append((S["col"][pos], S["val"][pos]))
+            return rows
+
+        mp.setattr(sell, "sell_from_csr", build)
+        mp.setattr(sell, "sell_to_dense_rows", decode)
+    return patch
+
+
+def _adam_without_bias_correction(orig):
+    def f(P, G, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        state["t"] = state.get("t", 0) + 1
+        for k in P:
+            m = state.setdefault("m_" + k, np.zeros_like(P[k]))
+            v = state.setdefault("v_" + k, np.zeros_like(P[k]))
+            m[...] = beta1 * m + (1 - beta1) * G[k]
+            v[...] = beta2 * v + (1 - beta2) * G[k] ** 2
+            P[k] = P[k] - lr * m / (np.sqrt(v) + eps)
+        return P
+    return f
+
+
 _pair = np.array([[0, 1], [1, 0]], dtype=np.complex128)
 
 MUTANTS = {
@@ -262,6 +322,15 @@ MUTANTS = {
         lambda mp: mp.setattr(sell, "np", _NumpyArgsort(
             lambda a: np.lexsort((-np.arange(len(a)), a)))),   # ties: later row first
         [lambda: pins.test_sell_round_trip_and_sorting(32, 64)]),
+    "SELL slots row-major inside a chunk (decoder to match)": (
+        _sell_layout(row_major=True),
+        [pins.test_sell_hand_worked_example]),
+    "SELL padding slots pointing at column 0": (
+        _sell_layout(pad_col_zero=True),
+        [pins.test_sell_hand_worked_example]),
+    "Adam without the bias correction": (
+        _wrap(mlp, "adam_step", _adam_without_bias_correction),
+        [pins.test_adam_two_steps_known_answers]),
     "SVQB scaled by Theta^-1": (
         _wrap(svqb, "svqb", _svqb_theta_power(1.0)),
         [pins.test_svqb_orthonormal_same_span_and_refill]),

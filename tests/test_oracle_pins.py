@@ -276,6 +276,31 @@ def test_sell_round_trip_and_sorting(C, sigma):
     assert S["chunk_ptr"][-1] == sum(S["chunk_len"]) * C
 
 
+def _keyed(name):
+    out = {}
+    for row in _rows(name):
+        out[row[0]] = row[1:]
+    return out
+
+
+def test_sell_hand_worked_example():
+    """SELL-C-sigma arrays of a 7-row matrix at C = 2, sigma = 4, written out by
+    hand from the format's definition (tests/golden/sell_c2_sigma4.txt):
+    sorting scope, chunk widths, column-major slots inside a chunk, padding
+    column and value, the slot past the last row."""
+    g = _keyed("sell_c2_sigma4.txt")
+    rowptr = np.array(g["csr_rowptr"], dtype=np.int64)
+    col = np.array(g["csr_col"], dtype=np.int32)
+    val = np.array(g["csr_val"], dtype=np.float64)
+    S = sell.sell_from_csr(rowptr, col, val, 2, 4)
+    assert S["nchunks"] == 4
+    assert S["perm"].tolist() == [int(v) for v in g["perm"]]
+    assert S["chunk_len"].tolist() == [int(v) for v in g["chunk_len"]]
+    assert S["chunk_ptr"].tolist() == [int(v) for v in g["chunk_ptr"]]
+    assert S["col"].tolist() == [int(v) for v in g["col"]]
+    assert S["val"].tolist() == [float(v) for v in g["val"]]
+
+
 # ---------------------------------------------------------------- filter quality
 
 
@@ -583,10 +608,62 @@ def test_mlp_adam_reduces_loss_on_a_fittable_target():
     assert mlp.loss(P, X, T) < 0.2 * L_start
 
 
+def test_adam_two_steps_known_answers():
+    """Two Adam steps on three parameters against values worked by hand from
+    Kingma and Ba's Algorithm 1 (tests/golden/adam_two_steps.txt): the
+    bias-corrected moments and the parameters after each step."""
+    from fractions import Fraction
+    from oracle import mlp
+    rows = _rows("adam_two_steps.txt")
+    th0 = np.array([float(r[0]) for r in rows])
+    g1 = np.array([float(r[1]) for r in rows])
+    g2 = np.array([float(r[2]) for r in rows])
+    P, st = {"theta": th0.copy()}, {}
+    mlp.adam_step(P, {"theta": g1}, st, 0.1)
+    mh1 = st["m_theta"] / (1 - 0.9)
+    vh1 = st["v_theta"] / (1 - 0.999)
+    for k, r in enumerate(rows):
+        assert mh1[k] == pytest.approx(float(Fraction(r[3])), rel=1e-13)
+        assert vh1[k] == pytest.approx(float(Fraction(r[4])), rel=1e-12)
+        assert P["theta"][k] == pytest.approx(float(r[5]), rel=1e-14, abs=1e-15)
+    mlp.adam_step(P, {"theta": g2}, st, 0.1)
+    assert st["t"] == 2
+    for k, r in enumerate(rows):
+        assert P["theta"][k] == pytest.approx(float(r[8]), rel=1e-14, abs=1e-15)
+
+
 def test_chebfd_empty_window_terminates():
     """A window inside a spectral gap holds no eigenvalue: the iteration stops
-    with no pairs after two iterations without in-window Ritz values."""
+    with no pairs after two iterations without in-window Ritz values.  The
+    first iterations still show a few spurious in-window Ritz values (mixtures
+    of the eigenvectors at both edges of the gap, ghost-flagged); they leave
+    the window as the filter sharpens the block."""
     lam = np.concatenate([np.linspace(-1, -0.2, 300), np.linspace(0.2, 1, 300)])
     H = sp.diags(lam).tocsr()
     r = solve.chebfd(H, -1.01, 1.01, -0.05, 0.05, 16, 60, 1e-9, complex_values=False)
-    assert r["converged"] and len(r["theta"]) == 0 and r["iterations"] <= 4
+    assert r["converged"] and len(r["theta"]) == 0 and r["iterations"] <= 10
+    assert r["log"][-1]["in_window"] == r["log"][-2]["in_window"] == 0
+
+
+def test_chebfd_weak_filter_is_not_taken_for_an_empty_window():
+    """A filter too weak for the ghost rule (Sec. 3.1 step 7): flat-DOS diagonal
+    H (D = 400), window [-0.02, 0.02] with 8 eigenvalues, N_p = 30.  The
+    residuals fall by less than 10x per iteration, so the true pairs are
+    ghost-flagged for several successive iterations; that is no evidence of
+    an empty window.  The iteration goes on until every window eigenvalue
+    of the diagonal converges; with N_p = 20 and n_s = 32 it never converges
+    within the budget and says so instead of returning an empty window."""
+    D = 400
+    lam = -1.0 + 2.0 * np.arange(1, D + 1) / (D + 1)
+    H = sp.diags(lam).tocsr()
+    ew = lam[(lam >= -0.02) & (lam <= 0.02)]
+    assert len(ew) == 8
+    r = solve.chebfd(H, -1.001, 1.001, -0.02, 0.02, 64, 30, 1e-10, complex_values=False,
+                     max_iter=40)
+    ghosted = [l for l in r["log"][1:] if l["accepted"] == 0 and l["in_window"] > 0]
+    assert len(ghosted) >= 2
+    assert r["converged"] and len(r["theta"]) == 8
+    assert np.abs(np.sort(r["theta"]) - ew).max() <= 1e-10
+    r = solve.chebfd(H, -1.001, 1.001, -0.02, 0.02, 32, 20, 1e-10, complex_values=False,
+                     max_iter=12)
+    assert not r["converged"] and r["iterations"] == 12
