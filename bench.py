@@ -298,6 +298,100 @@ def bench_ensemble(pkg, workloads, dev, peak_gbs):
             "autotune_ms_per_step": ms_step_tune}
 
 
+def fp64_class_kernels(pkg, H, N, alpha, beta, a, b, delta, peaks, stream):
+    """The FP64-class Chebyshev steps of the plain and mixed solves on the
+    insulator, each against its own bound: the native complex128 step on the
+    FP64 pipe (146 flop per row-vector update, Sec. 4; peak = a cuBLAS DGEMM
+    measured here), and the double-float steps (SELL and matrix-free, 16 bytes
+    per complex entry) against HBM on their own algorithmic bytes.  A
+    double-float step's time is the difference of two filters of degree 12
+    and 36, divided by the 24 extra steps (the conversions and the two start
+    steps cancel)."""
+    import torch
+    out = {}
+    nb = 32
+    # measured FP64 peak: cuBLAS DGEMM 4096^3, best of 3
+    A = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    B = torch.randn_like(A)
+    torch.matmul(A, B)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.matmul(A, B)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    fp64_peak = 2.0 * 4096 ** 3 / best / 1e12
+    del A, B
+    U = torch.empty((N, nb), dtype=torch.complex128, device="cuda")
+    Wv = torch.empty_like(U)
+    Y = torch.zeros_like(U)
+    pkg.chebfd_random_block(U, ns_total=nb, seed=11)
+    pkg.chebfd_random_block(Wv, ns_total=nb, seed=12)
+    for _ in range(3):
+        pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, U, Wv, Y)
+    reps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(reps):
+        if i % 2 == 0:
+            pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, U, Wv, Y)
+        else:
+            pkg.chebfd_chebyshev_step(H, alpha, beta, 1e-3, Wv, U, Y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    flops = N * nb * 146.0
+    out["c128_step"] = {"kernel": "cheb_step_kernel (MODE_STEP, c128, n_b=32)", "bound": "fp64",
+                        "launch_us": t * 1e6, "flops_per_launch": flops,
+                        "achieved_tflops": flops / t / 1e12, "peak_tflops": fp64_peak,
+                        "peak_kind": "cuBLAS DGEMM 4096^3 measured in this run",
+                        "frac": flops / t / 1e12 / fp64_peak,
+                        "hbm_gbs": N * (13 * 20 + 5 * nb * 16) / t / 1e9}
+    del Y, Wv
+    X = U
+    gc12 = pkg.chebfd_window_coeffs(a, b, -delta, delta, 12, "lanczos", 2.0)
+    gc36 = pkg.chebfd_window_coeffs(a, b, -delta, delta, 36, "lanczos", 2.0)
+
+    def df_step_time():
+        pkg.chebfd_filter_block_df(H, alpha, beta, gc12, X)   # warm-up
+        times = []
+        for gc in (gc12, gc36):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            pkg.chebfd_filter_block_df(H, alpha, beta, gc, X)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        return (times[1] - times[0]) / 24.0
+
+    peak = peaks["hbm_gbs"]
+    t_df = df_step_time()
+    b_df = N * (13 * (16 + 4) + 5 * nb * 16)
+    out["df_sell_step"] = {"kernel": "cheb_df_kernel (MODE_STEP, double-float complex, n_b=32)",
+                           "bound": "hbm", "launch_us": t_df * 1e6, "bytes_per_launch": b_df,
+                           "achieved": b_df / t_df / 1e9, "frac": b_df / t_df / 1e9 / peak}
+    H.set_matrix_free(True)
+    try:
+        t_dff = df_step_time()
+    finally:
+        H.set_matrix_free(False)
+    b_dff = N * 5 * nb * 16
+    out["df_matrix_free_step"] = {
+        "kernel": "stencil_df_kernel (MODE_STEP, double-float complex, n_b=32)", "bound": "hbm",
+        "launch_us": t_dff * 1e6, "bytes_per_launch": b_dff, "achieved": b_dff / t_dff / 1e9,
+        "frac": b_dff / t_dff / 1e9 / peak}
+    out["peak_hbm_gbs"] = peak
+    return out
+
+
+DENSE_PHASES = ("gram", "block_gemm", "eigensolve", "hy", "residuals", "other")
+
+
 def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chiral=True,
                 precisions=("fp64", "mixed", "mixed_df"), matrix_free=False):
     """Wall time of the whole ChebFD solve (Sec. 3.1 steps 4-8) to residual
@@ -331,7 +425,14 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chir
                           "converged": r["converged"], "max_residual_over_normH":
                               float(r["res"].max() / normH) if r["nev"] else None,
                           "seconds_filter": r["seconds_filter"],
-                          "seconds_dense": r["seconds_dense"], "n_mvm": r["n_mvm"]})
+                          "seconds_dense": r["seconds_dense"], "n_mvm": r["n_mvm"],
+                          "dense_breakdown_seconds": {
+                              ph: sum(rec["seconds_" + ph] for rec in r["log"])
+                              for ph in DENSE_PHASES},
+                          "iterations_log": [
+                              {"fp64_filter": rec["fp64_filter"], "in_window": rec["in_window"],
+                               "ghosts": rec["ghosts"], "accepted": rec["accepted"],
+                               "res_max": rec["res_max"]} for rec in r["log"]]})
         if chiral and r["nev"]:
             # spec(H) = -spec(H) for the insulator: the window set is +- paired
             out[name]["chiral_pairing_error"] = float(np.abs(lam + lam[::-1]).max())
@@ -354,7 +455,6 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chir
         t0 = time.perf_counter()
         ns_m, Np_m, kern_m, nt = pkg.chebfd_choose_params(H, -delta, delta, mlp=net, a=a, b=b,
                                                           m_feat=mlp_train.M_FEAT)
-        ns_m = max(ns_m, int(np.ceil(nt / 4.0)) * 4 + 8)   # never fewer vectors than targets
         t_choose = time.perf_counter() - t0
         extra = {"ns": ns_m, "Np": Np_m, "kernel": kern_m, "kpm_n_target": nt,
                  "seconds_parameter_choice": t_choose}
@@ -501,13 +601,18 @@ def run_ours(args):
         H.set_matrix_free(True)
         t_mf = time_step()
         H.set_matrix_free(False)
+        # its own algorithmic bytes: the five vector streams, no matrix
+        vb = N * 5 * nb * S_v
         roof["matrix_free_kernel"] = {
             "kernel": "stencil_step_kernel (MODE_STEP, %s, n_b=%d)" % (dtype_name, nb),
-            "launch_us": t_mf * 1e6, "achieved": bytes_launch / t_mf / 1e9,
-            "frac": bytes_launch / t_mf / 1e9 / peaks["hbm_gbs"],
-            "vector_bytes_per_launch": N * 5 * nb * S_v,
-            "vector_gbs": N * 5 * nb * S_v / t_mf / 1e9}
+            "launch_us": t_mf * 1e6, "bytes_per_launch": vb, "achieved": vb / t_mf / 1e9,
+            "frac": vb / t_mf / 1e9 / peaks["hbm_gbs"],
+            "speedup_over_stored_matrix_step": t_launch / t_mf}
     del U, Wv, Y
+    if single and w["kind"] == "topi" and not args.no_fp64_kernels:
+        torch.cuda.empty_cache()
+        roof["fp64_kernels"] = fp64_class_kernels(pkg, H, N, alpha, beta, a, b, delta, peaks,
+                                                  stream)
 
     # ---- end to end through the C ABI with host buffers ------------------------
     Xh = torch.empty((N, ns), dtype=cdt, pin_memory=True)
@@ -570,6 +675,57 @@ def run_ours(args):
     return 0
 
 
+def run_profile(args):
+    """Short, self-contained launch sequences for an ncu capture (no timing):
+    `step`  five fused Chebyshev steps on the workload's lattice (n_b = --nb,
+            value type --precision, --form blocked | sell | free);
+    `df`    one double-float filter of degree 8 on --nb complex columns
+            (--form sell | free);
+    `solve` one ChebFD iteration (filter of degree 20, SVQB, Rayleigh-Ritz) on
+            the 32x32x32x4 insulator (N = 131072, W = 1, seed 1), n_s = 256,
+            --solve-precisions[0] (fp64 | mixed_df)."""
+    import torch
+
+    import paper_1510_04895_gb300 as pkg
+    from paper_1510_04895_gb300 import workloads
+    name = args.workload
+    w = dict(getattr(workloads, WORKLOADS[name]["spec"]))
+    if args.profile == "solve":
+        w.update(Lx=32, Ly=32, Lz=32)
+    H = pkg.chebfd_matrix_create_lattice(w["kind"], w["Lx"], w["Ly"], w.get("Lz", 1), t=w["t"],
+                                         m=w.get("m", 0.0), W=w["W"], seed=w["seed"],
+                                         also_single=True)
+    if args.form == "sell" and H.blocked_width:
+        H.set_blocked(False)
+    if args.form == "free":
+        H.set_matrix_free(True)
+    if args.profile == "df":
+        nb = args.nb or 32
+        X = torch.empty((H.n, nb), dtype=torch.complex128, device="cuda")
+        pkg.chebfd_random_block(X, ns_total=nb, seed=1)
+        gc = pkg.chebfd_window_coeffs(-4.3, 4.3, -0.1, 0.1, 8, "lanczos", 2.0)
+        pkg.chebfd_filter_block_df(H, 2.0 / 8.6, 0.0, gc, X)
+    elif args.profile == "solve":
+        pkg.chebfd_solve(H, -0.14, 0.14, 256, 20, eps=1e-9, kernel="lanczos",
+                         precision=args.solve_precisions[0], a=-4.2, b=4.2, max_iter=1, seed=0)
+    else:
+        single = args.precision in ("single", "c64", "r32")
+        cplx = w["kind"] != "graphene"
+        dt = ({True: torch.complex64, False: torch.complex128} if cplx else
+              {True: torch.float32, False: torch.float64})[single]
+        nb = args.nb or w["nb"]
+        U = torch.empty((H.n, nb), dtype=dt, device="cuda")
+        W = torch.empty_like(U)
+        Y = torch.zeros_like(U)
+        pkg.chebfd_random_block(U, ns_total=nb, seed=1)
+        pkg.chebfd_random_block(W, ns_total=nb, seed=2)
+        for _ in range(5):
+            pkg.chebfd_chebyshev_step(H, 0.24, 0.0, 1e-3, U, W, Y)
+    torch.cuda.synchronize()
+    print("profile target done")
+    return 0
+
+
 def main():
     p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     p.add_argument("--gpus", type=int, default=1)
@@ -586,10 +742,18 @@ def main():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--no-solve", action="store_true")
+    p.add_argument("--no-fp64-kernels", dest="no_fp64_kernels", action="store_true")
     p.add_argument("--solve-precisions", dest="solve_precisions", nargs="*",
                    default=["fp64", "mixed", "mixed_df"],
                    help="precisions of the time-to-solution runs (the MLP run is extra)")
+    p.add_argument("--profile", choices=["step", "df", "solve"], default=None,
+                   help="run a short launch sequence for an ncu capture and exit")
+    p.add_argument("--form", choices=["blocked", "sell", "free"], default="blocked",
+                   help="--profile: insulator step on the blocked copy, the SELL arrays, or "
+                        "matrix-free")
     args = p.parse_args()
+    if args.profile:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

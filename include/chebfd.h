@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define CHEBFD_ABI_VERSION 2
+#define CHEBFD_ABI_VERSION 3
 
 typedef enum chebfd_status {
     CHEBFD_OK = 0,
@@ -262,10 +262,12 @@ chebfd_status chebfd_filter_block_df(const chebfd_matrix* H, double alpha, doubl
  * device array of 68 MiB (64 MiB for the work vectors, 4 MiB of moment
  * partials, 256 bytes of counters) that every GPU loading the library keeps
  * until the process exits; the call itself allocates nothing.  Limit: the work
- * vectors need 2 * N * w * element_size bytes, w = the panel width (n_b
- * rounded up to 16 bytes, at most 64 complex / 128 real columns), so N * w <=
- * 4M complex64 or real-double entries (e.g. N = 65536 at n_b = 64 complex64);
- * larger requests return CHEBFD_EINVAL with a message naming the sizes.
+ * vectors need 2 * N * w * element_size <= 64 MiB, where w is the panel
+ * width: n_b capped at 32 columns for C128, 64 for C64, 128 for R64 and R32,
+ * rounded up to a multiple of 16 bytes.  Examples at the limit: N = 65536
+ * with n_b >= 32 C128 or n_b >= 64 C64 (both 16 bytes x 32 or 8 bytes x 64 =
+ * 512 bytes per row and vector), N = 65536 with n_b >= 64 R64.  Larger
+ * requests return CHEBFD_EINVAL with a message naming the sizes.
  * The first call on a device looks up the device address of the array
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls on a device share the array and it keeps the last call's
@@ -276,9 +278,10 @@ chebfd_status chebfd_filter_block_noalloc(const chebfd_matrix* H, double alpha, 
                                           const double* gc, int Np, void* X, int64_t ld, int nb,
                                           chebfd_dtype vdt, double* moments, void* stream);
 
-/* One fused Chebyshev step of Fig. ChebFD (the kernel that carries the filter,
- * lines "w = 2(alpha H + beta) u - w ; x = x + g_n c_n w"): W <- 2(alpha H +
- * beta) U - W and Y <- Y + c W in one pass, for device blocks U, W, Y of shape
+/* One fused Chebyshev step (Sec. 2.1 recurrence, Fig. ChebFD; the kernel that
+ * carries the filter): with U = T_{n-1}(A) X and W = T_{n-2}(A) X on entry,
+ * W <- 2(alpha H + beta) U - W = T_n(A) X and Y <- Y + c W in one pass, for
+ * device blocks U, W, Y of shape
  * N x nb with a common leading dimension ld (U must not alias W or Y).  nb is
  * limited to one row group (C128/C64: 64, R64/R32: 128 columns).
  * Asynchronous on `stream`. */
@@ -439,8 +442,12 @@ typedef struct chebfd_mlp chebfd_mlp;
  * at which the KPM count reaches n_s (Eq. DOS:search), N_p = N_0 S_w/delta'
  * (Eq. etafit) with N_0 of Tab. lanczoskernel at the window centre, Lanczos
  * kernel.  Otherwise the MLP's outputs (log N_p, log n_s, kernel logit) on the
- * features of chebfd_param_features (m_feat moments).  Results are HOST ints;
- * kernel is a chebfd_kernel.  Synchronizes. */
+ * features of chebfd_param_features (m_feat moments), kept inside the range
+ * the network was trained on (N_p within [1/2, 2] of the rule's, n_s within
+ * [2, 6] N_T).  Either way n_s is never below N_T + 8 rounded up to a
+ * multiple of 8 (fewer search vectors than targets cannot converge; the 8
+ * covers the KPM estimate's error).  Results are HOST ints; kernel is a
+ * chebfd_kernel.  Synchronizes. */
 chebfd_status chebfd_choose_params(const chebfd_matrix* H, double a, double b, double lam_lo,
                                    double lam_hi, chebfd_mlp* mlp, int m_feat, uint64_t seed,
                                    int* ns, int* Np, int* kernel, double* n_target,
@@ -530,8 +537,10 @@ typedef struct chebfd_result chebfd_result;
  * the previous iteration's pair nearest in theta is discarded.  Converged
  * when at least one pair is accepted and every accepted in-window pair has
  * residual <= eps ||H||, or (empty window) when two successive iterations
- * from the second on accept no pair; the restart block is the set of Ritz
- * vectors.
+ * from the second on have no Ritz value in the window at all, ghosts
+ * included (ghost-flagged pairs of a weak filter keep the iteration going
+ * and end in ENOCONV at max_iter if they never converge); the restart block
+ * is the set of Ritz vectors.
  * MIXED precision switches to FP64 filter sweeps once the largest accepted
  * residual exceeds 1e-9 ||H|| and fell by less than 2x in an iteration.
  * Result handle owned by the library (chebfd_result_destroy).  ENOCONV when
@@ -557,6 +566,36 @@ typedef struct chebfd_result_info {
 } chebfd_result_info;
 
 chebfd_status chebfd_result_get(const chebfd_result* r, chebfd_result_info* out);
+
+/* One record per iteration of chebfd_solve (the iteration log of Sec. 3.1
+ * steps 5-8, as Fig. ConvTopi tracks it): window and ghost counts of the
+ * convergence test, the residual range of the accepted pairs, the precision
+ * of the filter, and where the time went.  The dense seconds are CUDA-event
+ * times on the solve's stream, split into the tall Gram products (Y^H Y,
+ * Y^H H Y, and Z^H Z with harmonic pairs), the tall block products (Y T,
+ * Ritz vectors, H V), the n_s x n_s eigenproblems with their small products
+ * and host decisions, the products H Y, the residual norms, and anything
+ * else (the separate-call path after a rank drop). */
+typedef struct chebfd_iteration_info {
+    int32_t iteration;          /* 1-based */
+    int32_t fp64_filter;        /* 1: the filter ran in FP64 (double-float in MIXED_DF), 0: single */
+    int32_t in_window;          /* Ritz values in [lam_lo, lam_hi] */
+    int32_t ghosts;             /* of them ghost-flagged */
+    int32_t accepted;           /* in-window pairs accepted (not ghosts) */
+    int32_t converged_pairs;    /* accepted pairs with residual <= eps ||H|| */
+    double res_min, res_max;    /* over the accepted pairs, absolute; -1 when none */
+    double seconds_filter;      /* host wall time of the filter (stream synchronized) */
+    double seconds_dense;       /* host wall time of steps 6-7 */
+    double seconds_gram, seconds_block_gemm, seconds_eigensolve, seconds_hy,
+        seconds_residuals, seconds_other;
+} chebfd_iteration_info;
+
+/* Copy up to `capacity` iteration records of a chebfd_solve result into the
+ * HOST array out (may be NULL when capacity is 0); *count (HOST) receives the
+ * number of records (= info.iterations).  Results of chebfd_solve_batched
+ * carry records with the counts and residuals but zero seconds. */
+chebfd_status chebfd_result_iterations(const chebfd_result* r, chebfd_iteration_info* out,
+                                       int capacity, int* count);
 
 /* Copy the accepted Ritz vectors (N x nev) into the caller's DEVICE buffer dst
  * (row-major, leading dimension ld >= nev, same FP64 type as the result).

@@ -99,6 +99,7 @@ SIGNATURES = {
     "chebfd_result_get": (ctypes.c_int, [c_vp, c_vp]),
     "chebfd_result_destroy": (ctypes.c_int, [c_vp]),
     "chebfd_result_copy_vectors": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int64, c_vp]),
+    "chebfd_result_iterations": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int, c_i32p]),
     "chebfd_ensemble_create": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_int,
                                               c_vp, ctypes.POINTER(c_vp)]),
     "chebfd_ensemble_info": (ctypes.c_int, [c_vp, c_i64p, c_i32p, c_i64p, c_i32p, c_i32p,
@@ -153,6 +154,17 @@ class ResultInfo(ctypes.Structure):
                 ("seconds_filter", ctypes.c_double), ("seconds_dense", ctypes.c_double),
                 ("seconds_total", ctypes.c_double), ("lambda_", c_dp), ("res", c_dp),
                 ("V", c_vp)]
+
+
+class IterationInfo(ctypes.Structure):
+    _fields_ = [("iteration", ctypes.c_int32), ("fp64_filter", ctypes.c_int32),
+                ("in_window", ctypes.c_int32), ("ghosts", ctypes.c_int32),
+                ("accepted", ctypes.c_int32), ("converged_pairs", ctypes.c_int32),
+                ("res_min", ctypes.c_double), ("res_max", ctypes.c_double),
+                ("seconds_filter", ctypes.c_double), ("seconds_dense", ctypes.c_double),
+                ("seconds_gram", ctypes.c_double), ("seconds_block_gemm", ctypes.c_double),
+                ("seconds_eigensolve", ctypes.c_double), ("seconds_hy", ctypes.c_double),
+                ("seconds_residuals", ctypes.c_double), ("seconds_other", ctypes.c_double)]
 
 
 class ChebFDError(RuntimeError):
@@ -424,7 +436,6 @@ def chebfd_solve(H, lam_lo, lam_hi, ns, Np, eps=1e-9, kernel="lanczos", mu=2.0, 
     """Run ChebFD; returns a dict with lambda, res (numpy), V (torch, device) and the log.
     extraction="harmonic" uses harmonic Ritz pairs for the window centre;
     window_inset=f filters with the window narrowed by f of the half-width."""
-    import torch
     p = Params(lam_lo=lam_lo, lam_hi=lam_hi, eps=eps, a=a, b=b, mu=mu, ns=ns, Np=Np,
                kernel=KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel), nb=nb,
                precision=PRECISION[precision], max_iter=max_iter,
@@ -434,25 +445,22 @@ def chebfd_solve(H, lam_lo, lam_hi, ns, Np, eps=1e-9, kernel="lanczos", mu=2.0, 
     st = lib().chebfd_solve(H.handle, ctypes.byref(p), _stream(stream), ctypes.byref(h))
     if st not in (0, 5) or not h:
         _check(st, "chebfd_solve")
-    info = ResultInfo()
     try:
-        _check(lib().chebfd_result_get(h, ctypes.byref(info)), "chebfd_result_get")
-        nev = info.nev
-        lam = np.ctypeslib.as_array(info.lambda_, (nev,)).copy() if nev else np.zeros(0)
-        res = np.ctypeslib.as_array(info.res, (nev,)).copy() if nev else np.zeros(0)
-        dt = torch.complex128 if H.is_complex else torch.float64
-        V = torch.empty((H.n, max(nev, 1)), dtype=dt, device="cuda")[:, :nev]
-        if nev:
-            _check(lib().chebfd_result_copy_vectors(h, _ptr(V), V.stride(0), _stream(stream)),
-                   "chebfd_result_copy_vectors")
-        out = dict(lam=lam, res=res, V=V, nev=nev, iterations=info.iterations,
-                   converged=bool(info.converged), fp64_iterations=info.fp64_iterations,
-                   n_mvm=info.n_mvm, a=info.a, b=info.b, seconds_filter=info.seconds_filter,
-                   seconds_dense=info.seconds_dense, seconds_total=info.seconds_total,
-                   status=STATUS[st])
+        return _result_dict(h, H.n, H.is_complex, st=st, stream=stream)
     finally:
         lib().chebfd_result_destroy(h)
-    return out
+
+
+def _iterations(h):
+    """The per-iteration records of a result handle, as a list of dicts."""
+    cnt = ctypes.c_int32()
+    _check(lib().chebfd_result_iterations(h, None, 0, ctypes.byref(cnt)),
+           "chebfd_result_iterations")
+    recs = (IterationInfo * max(cnt.value, 1))()
+    _check(lib().chebfd_result_iterations(h, recs, cnt.value, ctypes.byref(cnt)),
+           "chebfd_result_iterations")
+    return [{f: getattr(recs[i], f) for f, _ in IterationInfo._fields_}
+            for i in range(cnt.value)]
 
 
 class Ensemble:
@@ -525,7 +533,7 @@ def chebfd_ensemble_autotune(matrices, X, stream=None):
     return Ensemble(h), ms.value
 
 
-def _result_dict(h, n, is_complex, st=0, vectors=True):
+def _result_dict(h, n, is_complex, st=0, vectors=True, stream=None):
     import torch
     info = ResultInfo()
     _check(lib().chebfd_result_get(h, ctypes.byref(info)), "chebfd_result_get")
@@ -537,13 +545,13 @@ def _result_dict(h, n, is_complex, st=0, vectors=True):
         dt = torch.complex128 if is_complex else torch.float64
         V = torch.empty((n, max(nev, 1)), dtype=dt, device="cuda")[:, :nev]
         if nev:
-            _check(lib().chebfd_result_copy_vectors(h, _ptr(V), V.stride(0), _stream(None)),
+            _check(lib().chebfd_result_copy_vectors(h, _ptr(V), V.stride(0), _stream(stream)),
                    "chebfd_result_copy_vectors")
     return dict(lam=lam, res=res, V=V, nev=nev, iterations=info.iterations,
                 converged=bool(info.converged), fp64_iterations=info.fp64_iterations,
                 n_mvm=info.n_mvm, a=info.a, b=info.b, seconds_filter=info.seconds_filter,
                 seconds_dense=info.seconds_dense, seconds_total=info.seconds_total,
-                status=STATUS[st])
+                status=STATUS[st], log=_iterations(h))
 
 
 def chebfd_solve_batched(E, matrices, a, b, lam_lo, lam_hi, ns, Np, eps=1e-9, kernel="lanczos",

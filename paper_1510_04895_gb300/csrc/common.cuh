@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/chebfd.h"
 
@@ -188,6 +189,63 @@ SiteOrder site_order_of(const Matrix& M, int wc);
 void launch_step(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs& a,
                  cudaStream_t stream);
 int max_panel_width(chebfd_dtype dt);
+
+// Phases of the dense steps (Sec. 3.1 steps 6-7) timed with CUDA events on the
+// solve's stream: tall Gram products, tall block products, the n_s x n_s
+// eigenproblems with their small products and host decisions, the products
+// H Y, the residual norms, and anything else (rank-drop fallbacks).
+enum DensePhase { PH_GRAM = 0, PH_BLOCK_GEMM, PH_EIG, PH_HY, PH_RESIDUAL, PH_OTHER, PH_COUNT };
+
+// Records an event at each phase boundary; collect() waits for the last one
+// and adds each segment's time to acc[phase].  acc == nullptr: no events.
+class PhaseClock {
+  public:
+    PhaseClock(cudaStream_t s, double* acc) : s_(s), acc_(acc) { record(-1); }
+    ~PhaseClock() { release(); }
+    PhaseClock(const PhaseClock&) = delete;
+    PhaseClock& operator=(const PhaseClock&) = delete;
+    // the work enqueued since the previous mark belongs to `phase`
+    void mark(int phase) { record(phase); }
+    void collect() {
+        if (!acc_ || ev_.size() < 2) return;
+        CHEBFD_CHECK_CUDA(cudaEventSynchronize(ev_.back()));
+        for (size_t i = 1; i < ev_.size(); ++i) {
+            float ms = 0.f;
+            CHEBFD_CHECK_CUDA(cudaEventElapsedTime(&ms, ev_[i - 1], ev_[i]));
+            acc_[ph_[i]] += 1e-3 * ms;
+        }
+        release();
+        record(-1);
+    }
+
+  private:
+    void record(int phase) {
+        if (!acc_) return;
+        cudaEvent_t e = nullptr;
+        CHEBFD_CHECK_CUDA(cudaEventCreate(&e));
+        ev_.push_back(e);
+        ph_.push_back(phase);
+        CHEBFD_CHECK_CUDA(cudaEventRecord(e, s_));
+    }
+    void release() {
+        for (cudaEvent_t e : ev_) cudaEventDestroy(e);
+        ev_.clear();
+        ph_.clear();
+    }
+    cudaStream_t s_;
+    double* acc_;
+    std::vector<cudaEvent_t> ev_;
+    std::vector<int> ph_;
+};
+
+// One panel (nb <= max_panel_width) of p[H] X by the Chebyshev recurrence:
+// X (ld) becomes sum_n gc[n] T_n(A) X; U, W are two work panels (ldw);
+// moments (nullable, 2 Np x mom_ld) with per-block partials and a completion
+// counter that starts at zero.  Asynchronous on s.
+void filter_panel(const Matrix& M, double alpha, double beta, const double* gc, int Np, char* X,
+                  int64_t ld, int nb, chebfd_dtype dt, double* moments, int64_t mom_ld,
+                  char* U, char* W, int64_t ldw, double* partials, unsigned int* counter,
+                  cudaStream_t s);
 
 void launch_random_block(void* X, int64_t n, int64_t ld, int nb, int col0, int ns_total,
                          uint64_t seed, chebfd_dtype dt, cudaStream_t stream);

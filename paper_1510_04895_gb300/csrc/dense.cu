@@ -526,7 +526,10 @@ void gemm_small(Handles& h, bool cplx, bool ah, int ns, const double* A, const d
 template <class Gram, class Gemm>
 void harmonic_extract(const Matrix& M, double* Y, int64_t ld, int ns, bool cplx, double tau,
                       Handles& h, Gram&& tall_gram, Gemm&& tall_gemm, double* theta_host,
-                      double* res_host, cudaStream_t s) {
+                      double* res_host, cudaStream_t s, PhaseClock* clk = nullptr) {
+    auto mark = [&](int ph) {
+        if (clk) clk->mark(ph);
+    };
     const size_t es = cplx ? 16 : 8;
     const int64_t n = M.n;
     const int ew = cplx ? 2 : 1;  // doubles per entry
@@ -534,8 +537,10 @@ void harmonic_extract(const Matrix& M, double* Y, int64_t ld, int ns, bool cplx,
         A0((size_t)ns * ns * es, s), K((size_t)ns * ns * es, s), w((size_t)ns * sizeof(double), s),
         dth((size_t)ns * sizeof(double), s), res((size_t)ns * sizeof(double), s);
     spmv_impl(M, 1.0, -tau, Y, Z.p, ld, ns, cplx ? CHEBFD_C128 : CHEBFD_R64, s);
+    mark(PH_HY);
     tall_gram(Z.as<double>(), Y, A.as<double>());
     tall_gram(Z.as<double>(), Z.as<double>(), K.as<double>());
+    mark(PH_GRAM);
     if (cplx) {
         hermitize_kernel<true><<<grid1d((int64_t)ns * ns), 256, 0, s>>>(A.as<double>(), ns);
         hermitize_kernel<true><<<grid1d((int64_t)ns * ns), 256, 0, s>>>(K.as<double>(), ns);
@@ -586,14 +591,17 @@ void harmonic_extract(const Matrix& M, double* Y, int64_t ld, int ns, bool cplx,
     }
     CHEBFD_CHECK_CUDA(cudaMemcpyAsync(A.p, En.data(), (size_t)ns * ns * es, cudaMemcpyHostToDevice, s));
     CHEBFD_CHECK_CUDA(cudaMemcpyAsync(dth.p, dh.data(), ns * sizeof(double), cudaMemcpyHostToDevice, s));
+    mark(PH_EIG);
     // V = Y conj(En) into T, Z conj(En) into Y, residuals, Y <- V
     tall_gemm(ns, A.as<double>(), Y, T.as<double>());
     tall_gemm(ns, A.as<double>(), Z.as<double>(), Y);
+    mark(PH_BLOCK_GEMM);
     residuals_from_blocks(cplx, Y, T.as<double>(), dth.as<double>(), n, ld, ns, res.as<double>(), s);
     copy_block(Y, ld, T.p, ld, n, ns, es, s);
     if (res_host)
         CHEBFD_CHECK_CUDA(cudaMemcpyAsync(res_host, res.p, ns * sizeof(double),
                                           cudaMemcpyDeviceToHost, s));
+    mark(PH_RESIDUAL);
     CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
     CHEBFD_CHECK_CUDA(cudaGetLastError());
 }
@@ -633,8 +641,9 @@ void harmonic_ritz_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dt
 // orthonormal basis Y2 = Y1 T2, formed explicitly, instead of Ritz pairs.
 void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype dt, uint64_t seed,
                    int64_t* refill_counter, double* theta_host, double* res_host, bool df,
-                   bool harmonic, double tau, cudaStream_t s) {
+                   bool harmonic, double tau, cudaStream_t s, double* phase_seconds) {
     check_fp64_block(dt, Yv, M.n, ns, ld);
+    PhaseClock clk(s, phase_seconds);
     const bool cplx = dt == CHEBFD_C128;
     CHEBFD_REQUIRE(cplx == M.complex_values, CHEBFD_EINVAL, "dtype does not match the matrix");
     const size_t es = cplx ? 16 : 8;
@@ -683,11 +692,13 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
         else
             form_transform_kernel<false><<<grid1d((int64_t)ns * r), 256, 0, s>>>(
                 S.as<double>(), d.as<double>(), th.as<double>(), ns, first, r, Mt.as<double>());
+        clk.mark(PH_EIG);
         return r;
     };
 
     // ---- pass 1: Y1 = Y T1 (+ refill) into T
     tall_gram(Y, Y, S.as<double>());
+    clk.mark(PH_GRAM);
     const int r1 = svqb_transform();
     tall_gemm(r1, Mt.as<double>(), Y, T.as<double>());
     if (r1 < ns) {
@@ -699,8 +710,10 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
                                                                        ns, counter, seed);
         counter += ns - r1;
     }
+    clk.mark(PH_BLOCK_GEMM);
     // ---- pass 2: T2 from Y1^H Y1, kept in Mt (stored conj(T2))
     tall_gram(T.as<double>(), T.as<double>(), S.as<double>());
+    clk.mark(PH_GRAM);
     const int r2 = svqb_transform();
     if (r2 < ns) {
         // rank drop after pass 1: the separate, up to three-pass path
@@ -713,14 +726,18 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
                              res_host, s);
         else
             rayleigh_ritz_impl(M, Y, ld, ns, dt, theta_host, res_host, nullptr, s);
+        clk.mark(PH_OTHER);
+        clk.collect();
         return;
     }
     if (harmonic) {
         // Y <- Y2 = Y1 conj(Mt)
         tall_gemm(ns, Mt.as<double>(), T.as<double>(), Y);
+        clk.mark(PH_BLOCK_GEMM);
         T.reset();
         harmonic_extract(M, Y, ld, ns, cplx, tau, h, tall_gram, tall_gemm, theta_host, res_host,
-                         s);
+                         s, &clk);
+        clk.collect();
         if (refill_counter) *refill_counter = counter;
         return;
     }
@@ -728,7 +745,9 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
     Buf HY((size_t)n * ld * es, s), G((size_t)ns * ns * es, s), W2((size_t)ns * ns * es, s),
         res((size_t)ns * sizeof(double), s);
     spmv_impl(M, 1.0, 0.0, T.p, HY.p, ld, ns, dt, s);
+    clk.mark(PH_HY);
     tall_gram(HY.as<double>(), T.as<double>(), G.as<double>());
+    clk.mark(PH_GRAM);
     // stored conj(A2) = Mt^H conj(A1) Mt with conj(A1) in G
     gemm_small(h, cplx, false, ns, G.as<double>(), Mt.as<double>(), W2.as<double>());
     gemm_small(h, cplx, true, ns, Mt.as<double>(), W2.as<double>(), G.as<double>());
@@ -739,16 +758,20 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
     heev(h, cplx, G.as<double>(), ns, th.as<double>(), s);
     // C = Mt E (stored conj of T2 S); V = Y1 conj(C), HV = HY1 conj(C)
     gemm_small(h, cplx, false, ns, Mt.as<double>(), G.as<double>(), W2.as<double>());
+    clk.mark(PH_EIG);
     tall_gemm(ns, W2.as<double>(), T.as<double>(), Y);
     tall_gemm(ns, W2.as<double>(), HY.as<double>(), T.as<double>());
+    clk.mark(PH_BLOCK_GEMM);
     residuals_from_blocks(cplx, T.as<double>(), Y, th.as<double>(), n, ld, ns, res.as<double>(), s);
     CHEBFD_CHECK_CUDA(cudaMemcpyAsync(theta_host, th.p, ns * sizeof(double),
                                       cudaMemcpyDeviceToHost, s));
     if (res_host)
         CHEBFD_CHECK_CUDA(cudaMemcpyAsync(res_host, res.p, ns * sizeof(double),
                                           cudaMemcpyDeviceToHost, s));
+    clk.mark(PH_RESIDUAL);
     CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
     CHEBFD_CHECK_CUDA(cudaGetLastError());
+    clk.collect();
     if (refill_counter) *refill_counter = counter;
 }
 

@@ -143,11 +143,11 @@ void filter_block_df_impl(const Matrix& M, double alpha, double beta, const doub
         a.alpha = alpha;
         a.beta = beta;
         a.ldg = a.ldw = a.ldy = ldc;
-        // u = A x
+        // T_1 = A T_0 with T_0 = the panel D, into U
         a.gather = D.p;
         a.w = U.p;
         launch_df(M, MODE_SPMV, a, wc, s);
-        // w = 2 A u - x ; x = g0c0 x + g1c1 u + g2c2 w
+        // T_2 = 2 A T_1 - T_0 into W; D becomes gc_0 T_0 + gc_1 T_1 + gc_2 T_2
         a.gather = U.p;
         a.w = W.p;
         a.y = D.p;
@@ -155,14 +155,15 @@ void filter_block_df_impl(const Matrix& M, double alpha, double beta, const doub
         a.c1 = gc[1];
         a.c2 = gc[2];
         launch_df(M, MODE_SECOND, a, wc, s);
-        void* u = U.p;
-        void* w = W.p;
+        // n = 3..Np: T_n = 2 A T_{n-1} - T_{n-2} overwrites T_{n-2}; D gains gc_n T_n
+        void* t_prev = U.p;
+        void* t_cur = W.p;
         for (int k = 3; k <= Np; ++k) {
-            std::swap(u, w);
-            a.gather = u;
-            a.w = w;
+            a.gather = t_cur;
+            a.w = t_prev;
             a.c0 = gc[k];
             launch_df(M, MODE_STEP, a, wc, s);
+            std::swap(t_prev, t_cur);
         }
         if (cplx)
             from_df_kernel<true><<<conv_grid(M.n * wc), 256, 0, s>>>((const float4*)D.p, ldc, M.n, pnb, Xp, ld);

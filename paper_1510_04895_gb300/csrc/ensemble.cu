@@ -359,6 +359,7 @@ void fill_result(chebfd_result* R, const std::vector<int>& acc, const std::vecto
                  size_t es, int iterations, bool converged, int fp64_its, int64_t n_mvm,
                  double a, double b, cudaStream_t s);
 chebfd_result* new_result();
+void set_iterations(chebfd_result* R, const std::vector<chebfd_iteration_info>& recs);
 
 // The ChebFD iteration of Sec. 3.1 for every member of an ensemble at once:
 // one ensemble filter per iteration (all members, one graph launch), then
@@ -428,6 +429,7 @@ void solve_batched_impl(chebfd_ensemble* E, const chebfd_matrix* const* Hs, cons
             bool done = false, stalled = false, prev_empty = false;
             double prev_worst = -1.0;
             std::vector<double> prev_theta, prev_res;
+            std::vector<chebfd_iteration_info> recs;
             int64_t refill = 0;
         };
         std::vector<State> st(count);
@@ -452,8 +454,10 @@ void solve_batched_impl(chebfd_ensemble* E, const chebfd_matrix* const* Hs, cons
                 rayleigh_ritz_impl(Mi, Yi, ld, ns, d64, theta.data(), res.data(), nullptr, s);
                 const double normH = std::max(std::fabs(av[i]), std::fabs(bv[i]));
                 std::vector<int> acc;
+                int in_window = 0;
                 for (int k = 0; k < ns; ++k) {
                     if (!(theta[k] >= p.lam_lo && theta[k] <= p.lam_hi)) continue;
+                    ++in_window;
                     bool ghost = false;
                     if (!S.prev_theta.empty()) {
                         int j = 0;
@@ -466,17 +470,32 @@ void solve_batched_impl(chebfd_ensemble* E, const chebfd_matrix* const* Hs, cons
                     }
                     if (!ghost) acc.push_back(k);
                 }
-                double worst = 0.0;
-                for (int k : acc) worst = std::max(worst, res[k]);
+                double worst = 0.0, best = -1.0;
+                chebfd_iteration_info rec{};
+                rec.iteration = it;
+                rec.fp64_filter = single_phase ? 0 : 1;
+                for (int k : acc) {
+                    worst = std::max(worst, res[k]);
+                    best = best < 0.0 ? res[k] : std::min(best, res[k]);
+                    if (res[k] <= p.eps * normH) ++rec.converged_pairs;
+                }
+                rec.in_window = in_window;
+                rec.accepted = (int)acc.size();
+                rec.ghosts = in_window - rec.accepted;
+                rec.res_min = best;
+                rec.res_max = acc.empty() ? -1.0 : worst;
+                S.recs.push_back(rec);
                 bool conv = !acc.empty() && worst <= p.eps * normH;
-                // empty window: two successive iterations (ghosts recognised) accept nothing
-                const bool empty_now = !S.prev_theta.empty() && acc.empty();
+                // empty window: two successive iterations (from the second on)
+                // without any Ritz value in the window, ghosts included
+                const bool empty_now = !S.prev_theta.empty() && in_window == 0;
                 const bool empty = empty_now && S.prev_empty;
                 S.prev_empty = empty_now;
                 if (empty || (conv && !single_phase)) {
                     outs[i] = new_result();
                     fill_result(outs[i], acc, theta, res, Yi, Mi.n, ld, dtype_size(d64), it, true,
                                 fp64_its, (int64_t)it * ns * p.Np, av[i], bv[i], s);
+                    set_iterations(outs[i], S.recs);
                     S.done = true;
                     --remaining;
                     continue;
@@ -494,6 +513,7 @@ void solve_batched_impl(chebfd_ensemble* E, const chebfd_matrix* const* Hs, cons
                     outs[i] = new_result();
                     fill_result(outs[i], acc, theta, res, Yi, Mi.n, ld, dtype_size(d64), it,
                                 false, fp64_its, (int64_t)it * ns * p.Np, av[i], bv[i], s);
+                    set_iterations(outs[i], S.recs);
                 }
             }
             if (single_phase && all_stalled) single_phase = false;

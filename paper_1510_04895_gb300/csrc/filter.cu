@@ -266,7 +266,12 @@ int64_t padded_ld(chebfd_dtype dt, int nb) {
     return ((nb + (int64_t)per - 1) / (int64_t)per) * (int64_t)per;
 }
 
-// One panel of the filter of Fig. ChebFD; U, W: workspace panels (ldw).
+}  // namespace
+
+// One panel of the filter p[H] X = sum_n g_n c_n T_n(A) X, A = alpha H + beta
+// (Sec. 2.1), evaluated by the Chebyshev three-term recurrence in the order of
+// Fig. ChebFD: U and W (workspace panels, leading dimension ldw) hold the two
+// most recent T_n(A) X, and the panel X itself becomes the accumulated sum.
 void filter_panel(const Matrix& M, double alpha, double beta, const double* gc, int Np, char* X,
                   int64_t ld, int nb, chebfd_dtype dt, double* moments, int64_t mom_ld,
                   char* U, char* W, int64_t ldw, double* partials, unsigned int* counter,
@@ -279,7 +284,7 @@ void filter_panel(const Matrix& M, double alpha, double beta, const double* gc, 
     a.counter = counter;
     a.moments = moments;
     a.mom_ld = mom_ld;
-    // Step 1: u = A x
+    // T_1 = A T_0 with T_0 = X, into U
     a.gather = X;
     a.ldg = ld;
     a.w = U;
@@ -288,7 +293,7 @@ void filter_panel(const Matrix& M, double alpha, double beta, const double* gc, 
     a.ldy = 0;
     a.mom_step = 1;
     launch_step(M, dt, MODE_SPMV, a, s);
-    // Step 2: w = 2 A u - x ; x = g0c0 x + g1c1 u + g2c2 w
+    // T_2 = 2 A T_1 - T_0 into W; the sum starts as gc_0 T_0 + gc_1 T_1 + gc_2 T_2 in X
     a.gather = U;
     a.ldg = ldw;
     a.w = W;
@@ -300,20 +305,19 @@ void filter_panel(const Matrix& M, double alpha, double beta, const double* gc, 
     a.c2 = gc[2];
     a.mom_step = 2;
     launch_step(M, dt, MODE_SECOND, a, s);
-    // Steps n = 3..Np: swap(w, u); w = 2 A u - w; x = x + gn cn w
-    char* u = U;
-    char* w = W;
+    // n = 3..Np: T_n = 2 A T_{n-1} - T_{n-2} overwrites the buffer of T_{n-2};
+    // the sum gains gc_n T_n in the same pass
+    char* t_prev = U;  // T_{n-2}
+    char* t_cur = W;   // T_{n-1}
     for (int n = 3; n <= Np; ++n) {
-        std::swap(u, w);
-        a.gather = u;
-        a.w = w;
+        a.gather = t_cur;
+        a.w = t_prev;  // T_{n-2} in, T_n out
         a.c0 = gc[n];
         a.mom_step = n;
         launch_step(M, dt, MODE_STEP, a, s);
+        std::swap(t_prev, t_cur);
     }
 }
-
-}  // namespace
 
 void filter_block_impl(const Matrix& M, double alpha, double beta, const double* gc, int Np,
                        void* X, int64_t ld, int nb, chebfd_dtype dt, double* moments,

@@ -14,6 +14,7 @@
 // last call left there; calls whose device work overlaps (two streams, two
 // host threads) race on it and must be serialised by the caller.
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -29,19 +30,25 @@ constexpr size_t kScratchBytes = kFlagBytes + kPartialBytes + kWorkBytes;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
+std::once_flag g_scratch_once[kMaxDevices];
 void* g_scratch_ptr[kMaxDevices] = {};
+cudaError_t g_scratch_err[kMaxDevices] = {};
 
-// Device address of g_scratch for the current device, looked up once per
-// device (the host-side name g_scratch is not a device address).
+// Device address of g_scratch for the current device (the host-side name
+// g_scratch is not a device address), looked up once per device with that
+// device current; the once_flag makes concurrent first calls from several
+// host threads well defined (one looks up, the others wait for it).
 unsigned char* scratch_for_current_device() {
     int dev = 0;
     CHEBFD_CHECK_CUDA(cudaGetDevice(&dev));
     CHEBFD_REQUIRE(dev >= 0 && dev < kMaxDevices, CHEBFD_EUNSUPPORTED, "device index too large");
-    if (!g_scratch_ptr[dev]) {
+    std::call_once(g_scratch_once[dev], [dev] {
         void* p = nullptr;
-        CHEBFD_CHECK_CUDA(cudaGetSymbolAddress(&p, g_scratch));
+        g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_scratch);
         g_scratch_ptr[dev] = p;
-    }
+    });
+    CHEBFD_CHECK_CUDA(g_scratch_err[dev]);
+    CHEBFD_REQUIRE(g_scratch_ptr[dev] != nullptr, CHEBFD_ECUDA, "no device address for the scratch");
     return (unsigned char*)g_scratch_ptr[dev];
 }
 
@@ -101,43 +108,9 @@ void filter_block_noalloc_impl(const Matrix& M, double alpha, double beta, const
         const int pnb = std::min(pw, nb - p0);
         CHEBFD_REQUIRE(((size_t)pnb * es) % 16 == 0, CHEBFD_EINVAL,
                        "panel width * element size must be a multiple of 16 bytes");
-        char* Xp = (char*)X + p0 * es;
-        StepArgs a{};
-        a.nb = pnb;
-        a.alpha = alpha;
-        a.beta = beta;
-        a.partials = partials;
-        a.counter = counter;
-        a.moments = moments ? moments + p0 : nullptr;
-        a.mom_ld = nb;
-        // u = A x
-        a.gather = Xp;
-        a.ldg = ld;
-        a.w = U;
-        a.ldw = ldw;
-        a.mom_step = 1;
-        launch_step(M, dt, MODE_SPMV, a, s);
-        // w = 2 A u - x ; x = g0c0 x + g1c1 u + g2c2 w
-        a.gather = U;
-        a.ldg = ldw;
-        a.w = W;
-        a.y = Xp;
-        a.ldy = ld;
-        a.c0 = gc[0];
-        a.c1 = gc[1];
-        a.c2 = gc[2];
-        a.mom_step = 2;
-        launch_step(M, dt, MODE_SECOND, a, s);
-        char* u = U;
-        char* w = W;
-        for (int n = 3; n <= Np; ++n) {
-            std::swap(u, w);
-            a.gather = u;
-            a.w = w;
-            a.c0 = gc[n];
-            a.mom_step = n;
-            launch_step(M, dt, MODE_STEP, a, s);
-        }
+        // the same panel recurrence as chebfd_filter_block, on the fixed scratch
+        filter_panel(M, alpha, beta, gc, Np, (char*)X + p0 * es, ld, pnb, dt,
+                     moments ? moments + p0 : nullptr, nb, U, W, ldw, partials, counter, s);
     }
     if (moments) {
         moment_check_kernel<<<64, 256, 0, s>>>(moments, 2 * Np, nb, nb, flag);

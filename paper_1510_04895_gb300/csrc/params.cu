@@ -71,12 +71,20 @@ Analysis analyse(const Matrix& M, double a, double b, double lo, double hi, uint
     return A;
 }
 
+// Never fewer search vectors than target vectors (Sec. 3.1 step 2 needs
+// N_S > N_T): at least the KPM estimate N_T plus 8 for its stochastic error,
+// rounded up to a multiple of 8, and at least 16.
+int ns_floor(const Analysis& A) {
+    const int f = (int)std::ceil((std::max(A.n_target, 0.0) + 8.0) / 8.0) * 8;
+    return std::max(16, std::min(f, 1024));
+}
+
 void heuristic(const Matrix& M, const Analysis& A, double lo, double hi, int* ns, int* Np,
                int* kernel) {
     // Sec. 3.1 step 2 / Sec. 2.4: N_S = 4 N_T (optimum for the linear DOS of
     // the insulator and graphene), a multiple of 8, at least 16
     int n_s = (int)std::ceil(4.0 * std::max(A.n_target, 1.0) / 8.0) * 8;
-    n_s = std::max(16, std::min(n_s, 1024));
+    n_s = std::max(ns_floor(A), std::min(n_s, 1024));
     // Step 3, Eq. DOS:search: the margin delta' at which the KPM count reaches N_S
     double d_lo = 0.0, d_hi = A.b - A.a;
     for (int it = 0; it < 60; ++it) {
@@ -171,7 +179,7 @@ chebfd_status chebfd_choose_params(const chebfd_matrix* H, double a, double b, d
         const double rs = std::exp(std::max(std::log(2.0), std::min(std::log(6.0), (double)z[1])));
         *Np = (int)std::max(8.0, std::min(20000.0, std::round(rp * np_rule)));
         const int n_s = (int)std::ceil(rs * std::max(A.n_target, 1.0) / 8.0) * 8;
-        *ns = std::max(16, std::min(n_s, 1024));
+        *ns = std::max(ns_floor(A), std::min(n_s, 1024));
         *kernel = z[2] > 0.f ? CHEBFD_KERNEL_LANCZOS : CHEBFD_KERNEL_JACKSON;
     });
 }

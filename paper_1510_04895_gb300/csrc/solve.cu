@@ -13,7 +13,7 @@ void filter_block_df_impl(const Matrix& M, double alpha, double beta, const doub
                           void* X, int64_t ld, int nb, cudaStream_t s);
 void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype dt, uint64_t seed,
                    int64_t* refill_counter, double* theta_host, double* res_host, bool df,
-                   bool harmonic, double tau, cudaStream_t s);
+                   bool harmonic, double tau, cudaStream_t s, double* phase_seconds);
 void harmonic_ritz_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype dt, double tau,
                         double* theta_host, double* res_host, cudaStream_t s);
 
@@ -45,6 +45,7 @@ void fill_result(chebfd_result* R, const std::vector<int>& acc, const std::vecto
 
 struct chebfd_result {
     chebfd_result_info info{};
+    std::vector<chebfd_iteration_info> iterations;
     std::vector<double> lambda, res;
     void* V = nullptr;
     int64_t n = 0;
@@ -153,14 +154,28 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
         CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
         double t1 = now();
         t_filter += t1 - t0;
+        chebfd_iteration_info rec{};
+        rec.iteration = it;
+        rec.fp64_filter = single_phase ? 0 : 1;
+        rec.seconds_filter = t1 - t0;
         // ---- steps 6-7: orthonormalise, Rayleigh-Ritz
+        double phase[PH_COUNT] = {0, 0, 0, 0, 0, 0};
         ortho_rr_impl(M, Y64.p, ld, ns, d64, p.seed, &refill, theta.data(), res.data(), df,
-                      harmonic, tau, s);
-        t_dense += now() - t1;
+                      harmonic, tau, s, phase);
+        rec.seconds_dense = now() - t1;
+        t_dense += rec.seconds_dense;
+        rec.seconds_gram = phase[PH_GRAM];
+        rec.seconds_block_gemm = phase[PH_BLOCK_GEMM];
+        rec.seconds_eigensolve = phase[PH_EIG];
+        rec.seconds_hy = phase[PH_HY];
+        rec.seconds_residuals = phase[PH_RESIDUAL];
+        rec.seconds_other = phase[PH_OTHER];
         // ---- step 8: window membership, ghosts, convergence
         acc_idx.clear();
+        int in_window = 0;
         for (int k = 0; k < ns; ++k) {
             if (!(theta[k] >= p.lam_lo && theta[k] <= p.lam_hi)) continue;
+            ++in_window;
             bool ghost = false;
             if (!prev_theta.empty()) {
                 int j = 0;
@@ -171,11 +186,23 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
             }
             if (!ghost) acc_idx.push_back(k);
         }
-        double worst = 0.0;
-        for (int k : acc_idx) worst = std::max(worst, res[k]);
+        double worst = 0.0, best = -1.0;
+        for (int k : acc_idx) {
+            worst = std::max(worst, res[k]);
+            best = best < 0.0 ? res[k] : std::min(best, res[k]);
+            if (res[k] <= p.eps * normH) ++rec.converged_pairs;
+        }
+        rec.in_window = in_window;
+        rec.accepted = (int)acc_idx.size();
+        rec.ghosts = in_window - rec.accepted;
+        rec.res_min = best;
+        rec.res_max = acc_idx.empty() ? -1.0 : worst;
+        R->iterations.push_back(rec);
         converged = !acc_idx.empty() && worst <= p.eps * normH;
-        // empty window: two successive iterations (ghosts recognised) accept nothing
-        const bool empty_now = !prev_theta.empty() && acc_idx.empty();
+        // empty window: two successive iterations (from the second on) without
+        // any Ritz value in the window, ghosts included; ghost-flagged pairs of a
+        // weak filter keep the iteration going
+        const bool empty_now = !prev_theta.empty() && in_window == 0;
         if (empty_now && prev_empty) {
             converged = true;
             break;
@@ -204,6 +231,10 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
 }
 
 chebfd_result* new_result() { return new chebfd_result(); }
+
+void set_iterations(chebfd_result* R, const std::vector<chebfd_iteration_info>& recs) {
+    R->iterations = recs;
+}
 
 // Copy the accepted Ritz pairs (columns acc of the row-major block Y) into R.
 void fill_result(chebfd_result* R, const std::vector<int>& acc, const std::vector<double>& theta,
@@ -330,6 +361,17 @@ chebfd_status chebfd_result_get(const chebfd_result* r, chebfd_result_info* out)
     return guarded([&] {
         CHEBFD_REQUIRE(r && out, CHEBFD_EINVAL, "null argument");
         *out = r->info;
+    });
+}
+
+chebfd_status chebfd_result_iterations(const chebfd_result* r, chebfd_iteration_info* out,
+                                       int capacity, int* count) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(r && count && capacity >= 0 && (out || capacity == 0), CHEBFD_EINVAL,
+                       "bad argument");
+        *count = (int)r->iterations.size();
+        const int m = std::min(capacity, *count);
+        for (int i = 0; i < m; ++i) out[i] = r->iterations[i];
     });
 }
 

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(built):
     L = built.lib()
     for n in declared_functions():
         getattr(L, n)
-    assert L.chebfd_abi_version() == 2
+    assert L.chebfd_abi_version() == 3
 
 
 def test_binding_covers_every_symbol(built):

@@ -71,9 +71,12 @@ class _FakeLib:
         if self.fail == key:
             raise self.ChebFDError("planted failure")
         lam = np.array([-0.1, -0.05, 0.05, 0.1])
+        rec = dict(fp64_filter=0, in_window=4, ghosts=0, accepted=4, res_max=1e-10,
+                   seconds_gram=0.1, seconds_block_gemm=0.1, seconds_eigensolve=0.1,
+                   seconds_hy=0.05, seconds_residuals=0.05, seconds_other=0.0)
         return dict(a=a, b=b, lam=lam, res=np.full(4, 1e-10), nev=4, iterations=5,
                     fp64_iterations=1, converged=True, seconds_filter=1.0, seconds_dense=0.5,
-                    n_mvm=5 * ns * Np)
+                    n_mvm=5 * ns * Np, log=[rec] * 5)
 
     def set_matrix_free(self, on):
         self.calls.append(dict(matrix_free=on))
@@ -109,6 +112,8 @@ def test_solve_forms_of_the_benchmark(monkeypatch, fail):
     assert [c["extraction"] for c in solves] == ["ritz", "ritz", "ritz", "harmonic", "harmonic"]
     assert solves[-1]["window_inset"] == 0.5 and solves[-1]["Np"] == 305
     assert fake.calls[-1] == dict(matrix_free=False)
+    assert out["fp64"]["dense_breakdown_seconds"]["gram"] == pytest.approx(0.5)
+    assert len(out["fp64"]["iterations_log"]) == 5
     if fail is None:
         assert out["mixed_df_mlp_matrix_free_harmonic_inset"]["Np"] == 305
         assert out["speedup_mixed_df_mlp_matrix_free_harmonic_inset_over_fp64"] > 0

@@ -228,3 +228,29 @@ def test_solve_reports_no_convergence():
     H = pkg.chebfd_matrix_create_lattice("topi", 4, 4, 4, W=0.5, seed=0)
     r = pkg.chebfd_solve(H, -0.2, 0.2, 16, 20, eps=1e-12, kernel="jackson", max_iter=1)
     assert r["status"] == "ENOCONV" and not r["converged"] and r["iterations"] == 1
+
+
+def test_solve_weak_filter_is_not_taken_for_an_empty_window():
+    """The oracle's weak-filter case through the C ABI: flat-DOS diagonal H
+    (D = 400), window [-0.02, 0.02] with 8 eigenvalues, N_p = 30, n_s = 64.
+    The true pairs are ghost-flagged for several iterations; the solve must
+    not stop with an empty "converged" window but find all 8 eigenvalues.
+    With N_p = 20, n_s = 32 and a budget of 12 iterations it reports ENOCONV.
+    A window inside a spectral gap still ends converged with no pairs."""
+    import scipy.sparse as sp
+    D = 400
+    lam = -1.0 + 2.0 * np.arange(1, D + 1) / (D + 1)
+    H = pkg.chebfd_matrix_create_csr(np.arange(D + 1), np.arange(D), lam)
+    ew = lam[(lam >= -0.02) & (lam <= 0.02)]
+    r = pkg.chebfd_solve(H, -0.02, 0.02, 64, 30, eps=1e-10, a=-1.001, b=1.001, max_iter=40)
+    assert r["converged"] and r["nev"] == 8
+    assert np.abs(np.sort(r["lam"]) - ew).max() <= 1e-10
+    ro = osolve.chebfd(sp.diags(lam).tocsr(), -1.001, 1.001, -0.02, 0.02, 64, 30, 1e-10,
+                       complex_values=False, max_iter=40)
+    assert ro["converged"] and abs(ro["iterations"] - r["iterations"]) <= 2
+    r = pkg.chebfd_solve(H, -0.02, 0.02, 32, 20, eps=1e-10, a=-1.001, b=1.001, max_iter=12)
+    assert r["status"] == "ENOCONV" and not r["converged"] and r["iterations"] == 12
+    gap = np.concatenate([np.linspace(-1, -0.2, 300), np.linspace(0.2, 1, 300)])
+    G = pkg.chebfd_matrix_create_csr(np.arange(601), np.arange(600), gap)
+    r = pkg.chebfd_solve(G, -0.05, 0.05, 16, 60, eps=1e-9, a=-1.01, b=1.01, max_iter=20)
+    assert r["converged"] and r["nev"] == 0 and r["iterations"] <= 12
