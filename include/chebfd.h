@@ -537,10 +537,12 @@ typedef struct chebfd_result chebfd_result;
  * the previous iteration's pair nearest in theta is discarded.  Converged
  * when at least one pair is accepted and every accepted in-window pair has
  * residual <= eps ||H||, or (empty window) when two successive iterations
- * from the second on have no Ritz value in the window at all, ghosts
- * included (ghost-flagged pairs of a weak filter keep the iteration going
- * and end in ENOCONV at max_iter if they never converge); the restart block
- * is the set of Ritz vectors.
+ * from the second on have no in-window pair that is accepted or still
+ * converging (its residual at most 0.9 of the previous iteration's nearest
+ * pair's): ghost-flagged pairs of a weak filter keep converging and keep the
+ * iteration going (ENOCONV at max_iter if they never get there), while the
+ * in-window Ritz values of a window without eigenvalues stagnate; the
+ * restart block is the set of Ritz vectors.
  * MIXED precision switches to FP64 filter sweeps once the largest accepted
  * residual exceeds 1e-9 ||H|| and fell by less than 2x in an iteration.
  * Result handle owned by the library (chebfd_result_destroy).  ENOCONV when

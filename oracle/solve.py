@@ -11,11 +11,14 @@ Readings of the paper taken here (the paper leaves them open):
   accepted in-window pair below eps ||H||; the window is closed,
   lam_lo <= theta <= lam_hi.  Step 8a holds vacuously for a window without
   eigenvalues; such a window is taken as empty once two successive
-  iterations (from the second on) have no Ritz value in the window at all,
-  ghosts included.  Ghost-flagged pairs do not count as evidence of an empty
-  window: with a weak filter (damping worse than 10x per iteration) the true
-  pairs are ghost-flagged until their residuals fall below sqrt(eps) ||H||,
-  and the iteration has to go on (or end unconverged at max_iter);
+  iterations (from the second on) have no in-window Ritz pair that is either
+  accepted or still converging, a pair converging when its residual fell to
+  at most 0.9 of the previous iteration's nearest pair's.  With a weak
+  filter (damping worse than 10x per iteration) the true pairs are
+  ghost-flagged but their residuals keep falling, so the iteration goes on
+  (or ends unconverged at max_iter); the in-window Ritz values of a window
+  without eigenvalues are mixtures of eigenvectors on both sides of it,
+  whose residuals stagnate;
 * restart (step 8b): the next search block is the full set of Ritz vectors,
   which spans the same space as the orthonormalised filtered block;
 * window_inset=f filters with the window W = 1 on [c - (1-f) d, c + (1-f) d]
@@ -74,15 +77,17 @@ def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
             theta, V, res = rr.rayleigh_ritz(H, Q)
         inwin = (theta >= lam_lo) & (theta <= lam_hi)
         ghost = np.zeros_like(inwin)
+        falling = np.zeros_like(inwin)
         if prev is not None:
             pth, pres = prev
             for k in np.nonzero(inwin)[0]:
                 j = int(np.argmin(np.abs(pth - theta[k])))
                 if res[k] > np.sqrt(eps) * normH and not (pres[j] >= 10.0 * res[k]):
                     ghost[k] = True
+                falling[k] = res[k] <= 0.9 * pres[j]
         acc = inwin & ~ghost
         converged = bool(acc.any()) and bool(np.all(res[acc] <= eps * normH))
-        empty_now = prev is not None and not inwin.any()
+        empty_now = prev is not None and not (acc | (inwin & falling)).any()
         if empty_now and prev_empty:
             converged = True
         prev_empty = empty_now

@@ -454,11 +454,11 @@ void solve_batched_impl(chebfd_ensemble* E, const chebfd_matrix* const* Hs, cons
                 rayleigh_ritz_impl(Mi, Yi, ld, ns, d64, theta.data(), res.data(), nullptr, s);
                 const double normH = std::max(std::fabs(av[i]), std::fabs(bv[i]));
                 std::vector<int> acc;
-                int in_window = 0;
+                int in_window = 0, live = 0;
                 for (int k = 0; k < ns; ++k) {
                     if (!(theta[k] >= p.lam_lo && theta[k] <= p.lam_hi)) continue;
                     ++in_window;
-                    bool ghost = false;
+                    bool ghost = false, falling = false;
                     if (!S.prev_theta.empty()) {
                         int j = 0;
                         for (int q = 1; q < ns; ++q)
@@ -467,8 +467,10 @@ void solve_batched_impl(chebfd_ensemble* E, const chebfd_matrix* const* Hs, cons
                                 j = q;
                         ghost = res[k] > std::sqrt(p.eps) * normH &&
                                 !(S.prev_res[j] >= 10.0 * res[k]);
+                        falling = res[k] <= 0.9 * S.prev_res[j];
                     }
                     if (!ghost) acc.push_back(k);
+                    if (!ghost || falling) ++live;
                 }
                 double worst = 0.0, best = -1.0;
                 chebfd_iteration_info rec{};
@@ -487,8 +489,8 @@ void solve_batched_impl(chebfd_ensemble* E, const chebfd_matrix* const* Hs, cons
                 S.recs.push_back(rec);
                 bool conv = !acc.empty() && worst <= p.eps * normH;
                 // empty window: two successive iterations (from the second on)
-                // without any Ritz value in the window, ghosts included
-                const bool empty_now = !S.prev_theta.empty() && in_window == 0;
+                // without an in-window pair that is accepted or still converging
+                const bool empty_now = !S.prev_theta.empty() && live == 0;
                 const bool empty = empty_now && S.prev_empty;
                 S.prev_empty = empty_now;
                 if (empty || (conv && !single_phase)) {

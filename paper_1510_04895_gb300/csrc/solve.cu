@@ -151,7 +151,7 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
                                   s, p.nb);
             ++fp64_its;
         }
-        CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+        check_step_errors(s);
         double t1 = now();
         t_filter += t1 - t0;
         chebfd_iteration_info rec{};
@@ -172,19 +172,21 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
         rec.seconds_other = phase[PH_OTHER];
         // ---- step 8: window membership, ghosts, convergence
         acc_idx.clear();
-        int in_window = 0;
+        int in_window = 0, live = 0;
         for (int k = 0; k < ns; ++k) {
             if (!(theta[k] >= p.lam_lo && theta[k] <= p.lam_hi)) continue;
             ++in_window;
-            bool ghost = false;
+            bool ghost = false, falling = false;
             if (!prev_theta.empty()) {
                 int j = 0;
                 for (int q = 1; q < ns; ++q)
                     if (std::fabs(prev_theta[q] - theta[k]) < std::fabs(prev_theta[j] - theta[k]))
                         j = q;
                 ghost = res[k] > std::sqrt(p.eps) * normH && !(prev_res[j] >= 10.0 * res[k]);
+                falling = res[k] <= 0.9 * prev_res[j];
             }
             if (!ghost) acc_idx.push_back(k);
+            if (!ghost || falling) ++live;
         }
         double worst = 0.0, best = -1.0;
         for (int k : acc_idx) {
@@ -200,9 +202,10 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
         R->iterations.push_back(rec);
         converged = !acc_idx.empty() && worst <= p.eps * normH;
         // empty window: two successive iterations (from the second on) without
-        // any Ritz value in the window, ghosts included; ghost-flagged pairs of a
-        // weak filter keep the iteration going
-        const bool empty_now = !prev_theta.empty() && in_window == 0;
+        // an in-window pair that is accepted or still converging (residual at
+        // most 0.9 of the previous nearest pair's): the ghost-flagged pairs of a
+        // weak filter keep converging, spurious in-window values stagnate
+        const bool empty_now = !prev_theta.empty() && live == 0;
         if (empty_now && prev_empty) {
             converged = true;
             break;
