@@ -151,7 +151,7 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
                                   s, p.nb);
             ++fp64_its;
         }
-        check_step_errors(s);
+        CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
         double t1 = now();
         t_filter += t1 - t0;
         chebfd_iteration_info rec{};
