@@ -358,6 +358,30 @@ chebfd_status chebfd_harmonic_ritz(const chebfd_matrix* H, void* Y, int64_t ld, 
 chebfd_status chebfd_residuals(const chebfd_matrix* H, const void* V, const double* theta,
                                int64_t ld, int k, chebfd_dtype vdt, double* res, void* stream);
 
+/* Methods of chebfd_gram. */
+typedef enum chebfd_gram_method {
+    CHEBFD_GRAM_FP64 = 0,          /* cuBLAS FP64 GEMM (DGEMM / ZGEMM) */
+    CHEBFD_GRAM_DOUBLE_FLOAT = 1,  /* the library's double-float kernel on the FP32 pipe */
+    CHEBFD_GRAM_TENSOR = 2         /* the library's split onto the bf16 tensor cores */
+} chebfd_gram_method;
+
+/* The tall Gram product of the orthonormalisation and Rayleigh-Ritz steps
+ * (Sec. 3.1 steps 6-7: S = Y^H Y and Y^H (H Y)): C[p + q m] = sum_i A[i,p]
+ * conj(B[i,q]) for device blocks A (N x m, lda) and B (N x m, ldb), row-major,
+ * R64 or C128; C is a DEVICE m x m array, column-major (for C128 interleaved
+ * complex).  The stored matrix is the complex conjugate of A^H B.
+ * CHEBFD_GRAM_TENSOR splits every column of A and B into 8 bf16 digit slices
+ * (a power-of-two column scale, a 56-bit fixed-point value, balanced base-128
+ * digits; Ozaki, Ogita, Oishi, Rump 2012), multiplies the 36 leading slice
+ * pairs with tcgen05.mma, sums the leading digit groups exactly in integers
+ * and returns FP64-accurate results (error comparable to an FP64 GEMM);
+ * it needs 2 m <= 2048 real columns (m <= 1024 complex) and 16 N m (32 N m
+ * complex, twice that when B != A) bytes of workspace from the stream-ordered
+ * allocator.  EINVAL on bad arguments; ETIMEOUT if the tensor-core kernel gave
+ * up a bounded wait for its pipeline.  Synchronizes. */
+chebfd_status chebfd_gram(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n,
+                          int m, chebfd_dtype dt, double* C, int method, void* stream);
+
 /* Y = X with a change of precision (R64 <-> R32, C128 <-> C64, or a copy);
  * device blocks N x nb with leading dimensions ldx, ldy; round to nearest. */
 chebfd_status chebfd_convert_block(const void* X, chebfd_dtype xdt, int64_t ldx, void* Y,

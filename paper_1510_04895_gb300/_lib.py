@@ -100,6 +100,8 @@ SIGNATURES = {
     "chebfd_result_destroy": (ctypes.c_int, [c_vp]),
     "chebfd_result_copy_vectors": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int64, c_vp]),
     "chebfd_result_iterations": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int, c_i32p]),
+    "chebfd_gram": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, ctypes.c_int64, ctypes.c_int64,
+                                   ctypes.c_int, ctypes.c_int, c_vp, ctypes.c_int, c_vp]),
     "chebfd_ensemble_create": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_int,
                                               c_vp, ctypes.POINTER(c_vp)]),
     "chebfd_ensemble_info": (ctypes.c_int, [c_vp, c_i64p, c_i32p, c_i64p, c_i32p, c_i32p,
@@ -358,6 +360,26 @@ def chebfd_filter_block_df(H, alpha, beta, gc, X, stream=None):
     _check(lib().chebfd_filter_block_df(H.handle, alpha, beta, gc.ctypes.data_as(c_dp), Np,
                                         _ptr(X), X.stride(0), nb, dtype_of(X), _stream(stream)),
            "chebfd_filter_block_df")
+
+
+GRAM_METHODS = {"fp64": 0, "double_float": 1, "tensor": 2}
+
+
+def chebfd_gram(A, B=None, method="tensor", stream=None):
+    """A^H B (m x m device tensor) for device blocks A, B (N x m, R64/C128):
+    the tall Gram product of steps 6-7 by cuBLAS FP64 ("fp64"), the
+    double-float kernel ("double_float") or the bf16 tensor-core split
+    ("tensor")."""
+    import torch
+    B = A if B is None else B
+    n, m = A.shape[0], A.shape[1]
+    assert B.shape[0] == n and B.shape[1] == m and A.dtype == B.dtype
+    C = torch.empty((m, m), dtype=A.dtype, device=A.device)
+    _check(lib().chebfd_gram(_ptr(A), A.stride(0), _ptr(B), B.stride(0), n, m, dtype_of(A),
+                             _ptr(C), GRAM_METHODS[method], _stream(stream)), "chebfd_gram")
+    # the library stores C[p + q m] = sum_i A[i,p] conj(B[i,q]) column-major: read
+    # row-major that is C_rm[q, p]; A^H B [p, q] = conj(C_rm[q, p])
+    return C.T.conj()
 
 
 def chebfd_chebyshev_step(H, alpha, beta, c, U, W, Y, stream=None):

@@ -28,6 +28,9 @@ void df_gram(bool cplx, const double* A, int64_t lda, const double* B, int64_t l
              int m, double* C, void* work, int sms, cudaStream_t s);
 void df_gemm(bool cplx, int r, int64_t n, int k, const double* Mt, int ldm, const double* Y,
              int64_t ldy, double* T, int64_t ldt, cudaStream_t s);
+void oz_gram(bool cplx, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n,
+             int m, double* C, int sms, cudaStream_t s);
+void check_oz_errors(cudaStream_t s);
 
 namespace {
 
@@ -655,11 +658,12 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
         T((size_t)n * ld * es, s);
     std::vector<double> hth(ns);
     int64_t counter = refill_counter ? *refill_counter : 0;
-    // tall products: cuBLAS FP64, or double-float kernels (df)
-    Buf dfwork(df ? df_gram_work_bytes(ns, M.num_sms) : 0, s);
+    // tall products: cuBLAS FP64, or (df) the Grams on the bf16 tensor cores
+    // (FP64-accurate split, oz_gram.cu) and the block products as
+    // double-float kernels
     auto tall_gram = [&](const double* A, const double* B, double* C) {
         if (df)
-            df_gram(cplx, A, ld, B, ld, n, ns, C, dfwork.p, M.num_sms, s);
+            oz_gram(cplx, A, ld, B, ld, n, ns, C, M.num_sms, s);
         else
             gemm_nh(h, cplx, ns, n, A, ld, B, ld, C, ns);
     };
@@ -737,6 +741,7 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
         T.reset();
         harmonic_extract(M, Y, ld, ns, cplx, tau, h, tall_gram, tall_gemm, theta_host, res_host,
                          s, &clk);
+        if (df) check_oz_errors(s);
         clk.collect();
         if (refill_counter) *refill_counter = counter;
         return;
@@ -771,6 +776,7 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
     clk.mark(PH_RESIDUAL);
     CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
     CHEBFD_CHECK_CUDA(cudaGetLastError());
+    if (df) check_oz_errors(s);
     clk.collect();
     if (refill_counter) *refill_counter = counter;
 }
@@ -820,3 +826,44 @@ void convert_block_impl(const void* X, chebfd_dtype xdt, int64_t ldx, void* Y, c
 }
 
 }  // namespace chebfd
+
+using namespace chebfd;
+
+extern "C" chebfd_status chebfd_gram(const void* A, int64_t lda, const void* B, int64_t ldb,
+                                     int64_t n, int m, chebfd_dtype dt, double* C, int method,
+                                     void* stream) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(A && B && C, CHEBFD_EINVAL, "null argument");
+        CHEBFD_REQUIRE(dt == CHEBFD_R64 || dt == CHEBFD_C128, CHEBFD_EINVAL,
+                       "the Gram product takes FP64 blocks (R64 or C128)");
+        CHEBFD_REQUIRE(n >= 1 && m >= 1 && lda >= m && ldb >= m, CHEBFD_EINVAL,
+                       "need n >= 1, m >= 1, lda >= m, ldb >= m");
+        CHEBFD_REQUIRE(n < (1LL << 31), CHEBFD_EINVAL, "N must be < 2^31");
+        const bool cplx = dt == CHEBFD_C128;
+        cudaStream_t s = as_stream(stream);
+        int dev = 0, sms = 0;
+        CHEBFD_CHECK_CUDA(cudaGetDevice(&dev));
+        CHEBFD_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        switch (method) {
+            case CHEBFD_GRAM_FP64: {
+                Handles& h = handles_for_current_device(s);
+                gemm_nh(h, cplx, m, n, (const double*)A, lda, (const double*)B, ldb, C, m);
+                break;
+            }
+            case CHEBFD_GRAM_DOUBLE_FLOAT: {
+                Buf work(df_gram_work_bytes(m, sms), s);
+                df_gram(cplx, (const double*)A, lda, (const double*)B, ldb, n, m, C, work.p, sms,
+                        s);
+                break;
+            }
+            case CHEBFD_GRAM_TENSOR:
+                oz_gram(cplx, (const double*)A, lda, (const double*)B, ldb, n, m, C, sms, s);
+                break;
+            default:
+                CHEBFD_REQUIRE(false, CHEBFD_EINVAL, "unknown Gram method");
+        }
+        CHEBFD_CHECK_CUDA(cudaGetLastError());
+        check_oz_errors(s);
+    });
+}
+

@@ -1,0 +1,618 @@
+// FP64-accurate tall Gram products C = A^H B (A, B: N x m blocks, FP64 real
+// or complex, row-major) on the bf16 tensor cores, by an Ozaki-type split
+// (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59 (2012)).  These are the Gram matrices
+// of the orthonormalisation and Rayleigh-Ritz steps (Sec. 3.1 steps 6-7).
+//
+// A complex block is the real N x 2m block of its interleaved parts, so one
+// real Gram G = A_r^T B_r (2m x 2m) gives every complex entry.  Each column
+// of A_r (and of B_r) is scaled by a power of two 2^e (|entries| < 2^e) and
+// written as a 56-bit fixed-point number, split into 8 balanced base-128
+// digits d_1..d_8 (d_1 in [-128, 128], the others in [-64, 63]); every digit
+// is an integer that bf16 holds exactly.  Then
+//     G = 2^(e_a + e_b - 14) sum_{g} 2^(-7 (g - 2)) sum_{i + j = g} D_i^T E_j
+// where D_i, E_j are the digit slices (N x 2m bf16).  Pairs with i + j <= 9
+// (36 of 64) are kept; the dropped ones are below 2^-56 of the leading term.
+//
+// The slice products run as tcgen05.mma (kind::f16, bf16 in, FP32 out) into
+// eight TMEM accumulators, one per group g = 2..9.  A product of two digits
+// is at most 2^14 and a group has at most 7 x 2^12 per row in magnitude, so
+// the groups g <= 6 stay exact integers in FP32 over 512 rows; every 512 rows
+// they are read out, combined exactly into an int64 per output and cleared.
+// The groups 7-9 (2^-35 and below) accumulate in FP32 over the whole range.
+// Each CTA owns a 128 x 64 tile of G and a range of rows; a last kernel adds
+// the ranges in a fixed order, applies the scales and forms the complex
+// entries.  Digits are formed from the FP64 bit pattern with integer
+// operations (FP64 arithmetic is slow on this GPU).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "bulk_pipe.cuh"
+#include "common.cuh"
+
+namespace chebfd {
+
+namespace {
+
+constexpr int OZ_SLICES = 8;      // digits per entry
+constexpr int OZ_GROUPS = 8;      // g = 2..9
+constexpr int OZ_EXACT = 5;       // g = 2..6: exact, flushed every OZ_CHUNK rows
+constexpr int OZ_BM = 128;        // tile rows (columns of A)
+constexpr int OZ_BN = 64;         // tile columns (columns of B)
+constexpr int OZ_BK = 64;         // rows per K-block (one 128-byte swizzle row of bf16)
+constexpr int OZ_CHUNK = 512;     // rows between flushes of the exact groups
+constexpr int OZ_A_STAGES = 5;    // ring of A slice tiles
+constexpr int OZ_THREADS = 320;   // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int64_t OZ_MAX_RANGE = (int64_t)1 << 18;  // rows per CTA (int64 head-room)
+
+constexpr int A_TILE_BYTES = OZ_BM * OZ_BK * 2;               // 16 KB
+constexpr int B_STACK_BYTES = OZ_SLICES * OZ_BN * OZ_BK * 2;  // 64 KB
+
+// ------------------------------------------------------------ tcgen05 / TMA
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, M = 128, bf16 inputs, FP32 accumulators.
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrives (once) on bar when every tcgen05.mma issued so far by this thread has completed.
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both
+// K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(OZ_BM >> 4) << 24);
+}
+
+// Shared-memory descriptor of a K-major operand in the 128-byte swizzled
+// layout the TMA writes (rows of 128 bytes, 8-row atoms of 1024 bytes).
+__device__ __forceinline__ uint64_t umma_desc_sw128(const void* smem) {
+    const uint64_t addr = smem_u32(smem);
+    uint64_t d = 0;
+    d |= (addr >> 4) & 0x3FFFull;            // start address
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: 8 rows x 128 bytes
+    d |= (uint64_t)1 << 46;                  // descriptor version
+    d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+    return d;
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Zeros into 32 consecutive columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_zero32(uint32_t taddr) {
+    const uint32_t z = 0;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+        "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// 3-D tiled TMA load of box {c0.., c1.., c2..} into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace
+
+namespace {
+
+// ------------------------------------------------------------ split into digits
+
+// emax[c] = largest biased FP64 exponent field in column c of the N x cols
+// block A (row-major, ldr doubles per row); atomically merged over blocks.
+// Columns are handled 256 at a time by the threads of a block, up to 2048.
+__global__ void oz_colexp_kernel(const double* __restrict__ A, int64_t n, int cols, int64_t ldr,
+                                 int* __restrict__ emax) {
+    int mx[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = blockIdx.x * per, r1 = min(n, r0 + per);
+    for (int64_t r = r0; r < r1; ++r) {
+        const unsigned long long* row = reinterpret_cast<const unsigned long long*>(A + r * ldr);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = threadIdx.x + 256 * q;
+            if (c < cols) mx[q] = max(mx[q], (int)((__ldg(row + c) >> 52) & 0x7FF));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int c = threadIdx.x + 256 * q;
+        if (c < cols && mx[q] > 0) atomicMax(emax + c, mx[q]);
+    }
+}
+
+// The 8 balanced base-128 digits of x / 2^(E - 1022) as a 56-bit fixed-point
+// number (E: the column's largest biased exponent field, so |x| < 2^(E-1022)).
+__device__ __forceinline__ void oz_digits(double x, int E, float* d) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    unsigned long long mant = bits & ((1ull << 52) - 1);
+    int e = ex;
+    if (ex == 0) e = 1; else mant |= 1ull << 52;   // subnormal: no implicit bit
+    // X = mant * 2^(e - E + 3) < 2^56, rounded to nearest when shifted right
+    const int sh = e - E + 3;
+    unsigned long long X;
+    if (sh >= 0)
+        X = mant << sh;
+    else if (-sh >= 60)
+        X = 0;
+    else
+        X = (mant + (1ull << (-sh - 1))) >> (-sh);
+    long long V = (long long)X;
+    if (bits >> 63) V = -V;
+#pragma unroll
+    for (int s = OZ_SLICES - 1; s >= 1; --s) {
+        const long long dv = ((V & 127) ^ 64) - 64;   // in [-64, 63]
+        d[s] = (float)dv;
+        V = (V - dv) >> 7;
+    }
+    d[0] = (float)V;                                  // in [-128, 128]
+}
+
+// S[s][c][k] (bf16, k contiguous, kpad rows per column) = digit s of A[k][c];
+// zero for n <= k < kpad.  A block takes 64 rows x 32 columns: lane = column
+// (coalesced reads of a row), each thread forms the digits of two consecutive
+// rows and keeps them as one 32-bit word per slice, so the transpose through
+// shared memory (33 words per column: conflict-free) and the global writes
+// (32 lanes x 4 bytes of one column) stay coalesced.
+__global__ void __launch_bounds__(256) oz_split_kernel(const double* __restrict__ A, int64_t n,
+                                                       int cols, int64_t ldr, const int* emax,
+                                                       int64_t kpad, uint32_t* __restrict__ S) {
+    __shared__ uint32_t t[OZ_SLICES][32][33];
+    const int64_t k0 = (int64_t)blockIdx.x * 64;
+    const int c0 = blockIdx.y * 32;
+    const int tc = threadIdx.x % 32, tw = threadIdx.x / 32;
+    const int c = c0 + tc;
+    const int E = c < cols ? emax[c] : 0;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int kp = tw + 8 * p;           // row pair 0..31 of the tile
+        const int64_t k = k0 + 2 * kp;
+        float d0[OZ_SLICES], d1[OZ_SLICES];
+        const double x0 = (c < cols && k < n) ? __ldg(A + k * ldr + c) : 0.0;
+        const double x1 = (c < cols && k + 1 < n) ? __ldg(A + (k + 1) * ldr + c) : 0.0;
+        oz_digits(x0, E, d0);
+        oz_digits(x1, E, d1);
+#pragma unroll
+        for (int s = 0; s < OZ_SLICES; ++s) {
+            const __nv_bfloat162 v = __floats2bfloat162_rn(d0[s], d1[s]);  // low half: row k
+            t[s][tc][kp] = *reinterpret_cast<const uint32_t*>(&v);
+        }
+    }
+    __syncthreads();
+    // per (slice, column): 32 words (64 rows) written by the 32 lanes of a warp
+    const size_t slice_stride = (size_t)cols * kpad / 2;   // in words
+    for (int q = tw; q < OZ_SLICES * 32; q += 8) {
+        const int s = q / 32, cc = q % 32;
+        if (c0 + cc >= cols) continue;
+        S[s * slice_stride + ((size_t)(c0 + cc) * kpad + k0) / 2 + tc] = t[s][cc][tc];
+    }
+}
+
+}  // namespace
+
+// Set when an Ozaki Gram kernel gave up a bounded wait; read by check_oz_errors().
+__device__ unsigned int g_oz_error = 0;
+
+namespace {
+
+struct OzSmem {
+    // 1024-byte aligned operand buffers first (the 128-byte swizzle atoms)
+    unsigned char b[2][B_STACK_BYTES];        // 8 B slices of one K-block, double buffered
+    unsigned char a[OZ_A_STAGES][A_TILE_BYTES];  // ring of single A slice tiles
+    uint64_t a_full[OZ_A_STAGES], a_empty[OZ_A_STAGES];
+    uint64_t b_full[2], b_empty[2];
+    uint64_t chunk_done;                      // MMAs of a 512-row chunk completed
+    uint64_t flushed;                         // epilogue has read and cleared the exact groups
+    uint32_t tmem_base;
+    uint32_t fail;                            // a bounded wait ran out somewhere in the CTA
+};
+
+__device__ __forceinline__ bool oz_wait(OzSmem& sm, uint64_t* bar, uint32_t parity) {
+    if (*(volatile uint32_t*)&sm.fail) return false;
+    if (mbar_wait(bar, parity)) return true;
+    atomicExch(&sm.fail, 1u);
+    atomicExch(&g_oz_error, kPipeErrTimeout);
+    return false;
+}
+
+// One CTA: the 128 x 64 tile (m0, n0) of G over the rows [k_begin, k_end)
+// (k_begin a multiple of OZ_CHUNK); writes its part to P[split][m][n] in units
+// of one group-2 digit product.
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    oz_gram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   int64_t rows_per_split, int64_t kpad, int cols_a, int cols_b,
+                   double* __restrict__ P) {
+    extern __shared__ unsigned char smem_raw[];
+    OzSmem& sm = *reinterpret_cast<OzSmem*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN, split = blockIdx.z;
+    const int64_t k_begin = split * rows_per_split;
+    const int64_t k_end = min(kpad, k_begin + rows_per_split);
+    const int nkb = (int)((k_end - k_begin) / OZ_BK);          // kpad is a multiple of OZ_BK
+    const int nchunks = (nkb + OZ_CHUNK / OZ_BK - 1) / (OZ_CHUNK / OZ_BK);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < OZ_A_STAGES; ++i) {
+            mbar_init(&sm.a_full[i], 1);
+            mbar_init(&sm.a_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sm.b_full[i], 1);
+            mbar_init(&sm.b_empty[i], 1);
+        }
+        mbar_init(&sm.chunk_done, 1);
+        mbar_init(&sm.flushed, 8);
+        sm.fail = 0;
+        mbar_init_fence();
+    }
+    if (warp == 1) {
+        tmem_alloc(&sm.tmem_base, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem_base;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        int issued_a = 0, issued_b = 0;
+        if (lane == 0) {
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int k = (int)(k_begin + (int64_t)kb * OZ_BK);
+                const int bs = kb & 1;
+                if (kb >= 2 && !oz_wait(sm, &sm.b_empty[bs], ((kb >> 1) - 1) & 1)) break;
+                mbar_arrive_expect_tx(&sm.b_full[bs], B_STACK_BYTES);
+                tma_load_3d(sm.b[bs], &tmB, k, n0, 0, &sm.b_full[bs]);
+                ++issued_b;
+                bool ok = true;
+                for (int i = 0; i < OZ_SLICES && ok; ++i) {
+                    const int q = kb * OZ_SLICES + i, as = q % OZ_A_STAGES;
+                    if (q >= OZ_A_STAGES && !oz_wait(sm, &sm.a_empty[as], ((q / OZ_A_STAGES) - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&sm.a_full[as], A_TILE_BYTES);
+                    tma_load_3d(sm.a[as], &tmA, k, m0, i, &sm.a_full[as]);
+                    ++issued_a;
+                }
+                if (!ok) break;
+            }
+            // every copy issued has landed before the CTA may end
+            for (int q = max(0, issued_a - OZ_A_STAGES); q < issued_a; ++q)
+                if (!mbar_wait(&sm.a_full[q % OZ_A_STAGES], (q / OZ_A_STAGES) & 1)) break;
+            for (int kb = max(0, issued_b - 2); kb < issued_b; ++kb)
+                if (!mbar_wait(&sm.b_full[kb & 1], (kb >> 1) & 1)) break;
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            bool ok = true;
+            int committed_chunks = 0;
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                const int c = kb / (OZ_CHUNK / OZ_BK);
+                if (kb % (OZ_CHUNK / OZ_BK) == 0 && !oz_wait(sm, &sm.flushed, c & 1)) break;
+                const int bs = kb & 1;
+                if (!oz_wait(sm, &sm.b_full[bs], (kb >> 1) & 1)) break;
+                tc_fence_after();
+                for (int i = 0; i < OZ_SLICES; ++i) {
+                    const int q = kb * OZ_SLICES + i, as = q % OZ_A_STAGES;
+                    if (!oz_wait(sm, &sm.a_full[as], (q / OZ_A_STAGES) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t adesc = umma_desc_sw128(sm.a[as]);
+                    // slice i+1 of A against slices j = 1 .. 8 - i of B: group i + j + 1,
+                    // TMEM columns 64 (i + j - 1), at most 4 slices (256 columns) per MMA
+                    for (int j0 = 1; j0 <= OZ_SLICES - i; j0 += 4) {
+                        const int nj = min(4, OZ_SLICES - i - j0 + 1);
+                        const uint64_t bdesc =
+                            umma_desc_sw128(sm.b[bs] + (size_t)(j0 - 1) * OZ_BN * OZ_BK * 2);
+                        const uint32_t d = tmem + (uint32_t)(OZ_BN * (i + j0 - 1));
+                        const uint32_t idesc = umma_idesc_bf16(OZ_BN * nj);
+#pragma unroll
+                        for (int ks = 0; ks < OZ_BK / 16; ++ks)
+                            // 16 rows of K = 32 bytes along the swizzled 128-byte row
+                            umma_bf16(d, adesc + 2 * ks, bdesc + 2 * ks, idesc, 1u);
+                    }
+                    umma_commit(&sm.a_empty[as]);
+                }
+                if (!ok) break;
+                umma_commit(&sm.b_empty[bs]);
+                if (kb % (OZ_CHUNK / OZ_BK) == OZ_CHUNK / OZ_BK - 1 || kb == nkb - 1) {
+                    umma_commit(&sm.chunk_done);
+                    ++committed_chunks;
+                }
+            }
+            // the MMAs in flight finish before TMEM is released: wait for the
+            // last chunk commit (issued after every MMA)
+            if (committed_chunks > 0)
+                mbar_wait(&sm.chunk_done, (committed_chunks - 1) & 1);
+        }
+    } else {
+        // ---------------- epilogue: warps 2..9
+        const int quarter = warp % 4;              // TMEM lanes 32*quarter.. (hardware rule)
+        const int half = (warp - 2) / 4;           // columns 32*half..32*half+31 of each group
+        const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+        auto col_addr = [&](int g) { return tmem + lane_base + (uint32_t)(OZ_BN * g + 32 * half); };
+        for (int g = 0; g < OZ_GROUPS; ++g) tmem_zero32(col_addr(g));
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.flushed);
+        long long T[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) T[j] = 0;
+        bool ok = true;
+        for (int c = 0; c < nchunks && ok; ++c) {
+            bool got = true;
+            if (lane == 0) got = oz_wait(sm, &sm.chunk_done, c & 1);
+            ok = __shfl_sync(0xffffffffu, got, 0);
+            if (!ok) break;
+            tc_fence_after();
+#pragma unroll
+            for (int g = 0; g < OZ_EXACT; ++g) {
+                float v[32];
+                tmem_ld32(col_addr(g), v);
+                const int sh = 7 * (OZ_EXACT - 1 - g);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) T[j] += (long long)__float2int_rn(v[j]) * (1ll << sh);
+                tmem_zero32(col_addr(g));
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.flushed);
+        }
+        if (ok) {
+            float t7[32], t8[32], t9[32];
+            tmem_ld32(col_addr(OZ_EXACT), t7);
+            tmem_ld32(col_addr(OZ_EXACT + 1), t8);
+            tmem_ld32(col_addr(OZ_EXACT + 2), t9);
+            const int m = m0 + 32 * quarter + lane;
+            if (m < cols_a) {
+                double* out = P + ((size_t)split * cols_a + m) * cols_b;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int n = n0 + 32 * half + j;
+                    if (n < cols_b)
+                        out[n] = ldexp((double)T[j], -28) + ldexp((double)t7[j], -35) +
+                                 ldexp((double)t8[j], -42) + ldexp((double)t9[j], -49);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
+// C (m x m, column-major, ldc) from the split partials: the fixed-order sum
+// over splits, the column scales 2^(E_a - 1022) 2^(E_b - 1022) 2^-14, and for
+// complex blocks the combination of the four real parts of each entry:
+//     C[p + q ldc] = sum_i A[i,p] conj(B[i,q]).
+__global__ void oz_finish_kernel(const double* __restrict__ P, int nsplit, int cols, int m,
+                                 bool cplx, const int* ea, const int* eb, double* __restrict__ C,
+                                 int ldc) {
+    const int total = m * m;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int p = t % m, q = t / m;
+        auto g = [&](int r, int c) {
+            double s = 0.0;
+            for (int k = 0; k < nsplit; ++k) s += P[((size_t)k * cols + r) * cols + c];
+            const int e = (ea[r] > 0 ? ea[r] - 1022 : 0) + (eb[c] > 0 ? eb[c] - 1022 : 0) - 14;
+            return ldexp(s, e);
+        };
+        if (cplx) {
+            const double re = g(2 * p, 2 * q) + g(2 * p + 1, 2 * q + 1);
+            const double im = g(2 * p + 1, 2 * q) - g(2 * p, 2 * q + 1);
+            C[2 * ((size_t)p + (size_t)q * ldc)] = re;
+            C[2 * ((size_t)p + (size_t)q * ldc) + 1] = im;
+        } else {
+            C[(size_t)p + (size_t)q * ldc] = g(p, q);
+        }
+    }
+}
+
+}  // namespace
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    CHEBFD_REQUIRE(fn != nullptr, CHEBFD_ECUDA, "cuTensorMapEncodeTiled is not available");
+    return fn;
+}
+
+// Tensor map of the digit slices S[8][cols][kpad] (bf16): box of OZ_BK rows x
+// `rows` columns x `slices` slices, 128-byte swizzle (the layout the MMA
+// descriptors expect), zero fill outside the block.
+CUtensorMap slice_map(const __nv_bfloat16* S, int64_t kpad, int cols, int rows, int slices) {
+    CUtensorMap m;
+    const cuuint64_t dim[3] = {(cuuint64_t)kpad, (cuuint64_t)cols, (cuuint64_t)OZ_SLICES};
+    const cuuint64_t stride[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)cols * kpad * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)rows, (cuuint32_t)slices};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    const CUresult r = encode_tiled()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                                      const_cast<__nv_bfloat16*>(S), dim, stride, box, estride,
+                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CHEBFD_REQUIRE(r == CUDA_SUCCESS, CHEBFD_ECUDA,
+                   "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return m;
+}
+
+struct OzBuf {
+    void* p = nullptr;
+    cudaStream_t s;
+    OzBuf(size_t bytes, cudaStream_t st) : s(st) {
+        if (bytes) CHEBFD_CHECK_CUDA(cudaMallocAsync(&p, bytes, st));
+    }
+    ~OzBuf() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    OzBuf(const OzBuf&) = delete;
+    OzBuf& operator=(const OzBuf&) = delete;
+};
+
+// Column exponents and digit slices of one real N x cols block.
+void oz_prepare(const double* A, int64_t n, int cols, int64_t ldr, int64_t kpad, int* emax,
+                __nv_bfloat16* S, int sms, cudaStream_t s) {
+    CHEBFD_CHECK_CUDA(cudaMemsetAsync(emax, 0, (size_t)cols * sizeof(int), s));
+    const int g = (int)std::min<int64_t>((int64_t)sms * 8, std::max<int64_t>(1, n / 64));
+    oz_colexp_kernel<<<g, 256, 0, s>>>(A, n, cols, ldr, emax);
+    const dim3 grid((unsigned)(kpad / 64), (unsigned)((cols + 31) / 32));
+    oz_split_kernel<<<grid, 256, 0, s>>>(A, n, cols, ldr, emax, kpad,
+                                         reinterpret_cast<uint32_t*>(S));
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+size_t oz_gram_smem_bytes() { return sizeof(OzSmem) + 1024; }
+
+// C (m x m, column-major, ld m) = A^T conj(B) summed over the N rows, i.e.
+// C[p + q m] = sum_i A[i,p] conj(B[i,q]) for row-major N x m blocks A (lda) and
+// B (ldb), FP64 real or complex (interleaved); B == A is recognised and split
+// once.  Asynchronous on s; workspace from the stream-ordered allocator.
+void oz_gram(bool cplx, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n,
+             int m, double* C, int sms, cudaStream_t s) {
+    const int cols = cplx ? 2 * m : m;
+    const int64_t ldra = cplx ? 2 * lda : lda, ldrb = cplx ? 2 * ldb : ldb;
+    CHEBFD_REQUIRE(cols >= 1 && cols <= 2048, CHEBFD_EINVAL, "Ozaki Gram: at most 2048 real columns");
+    CHEBFD_REQUIRE(n >= 1, CHEBFD_EINVAL, "Ozaki Gram: empty block");
+    const int64_t kpad = (n + OZ_BK - 1) / OZ_BK * OZ_BK;
+    const bool same = A == B && lda == ldb;
+    const size_t slice_bytes = (size_t)OZ_SLICES * cols * kpad * sizeof(__nv_bfloat16);
+    OzBuf ea((size_t)cols * sizeof(int), s), eb(same ? 0 : (size_t)cols * sizeof(int), s);
+    OzBuf sa(slice_bytes, s), sb(same ? 0 : slice_bytes, s);
+    oz_prepare(A, n, cols, ldra, kpad, (int*)ea.p, (__nv_bfloat16*)sa.p, sms, s);
+    if (!same) oz_prepare(B, n, cols, ldrb, kpad, (int*)eb.p, (__nv_bfloat16*)sb.p, sms, s);
+    const int* eB = same ? (const int*)ea.p : (const int*)eb.p;
+    const __nv_bfloat16* SB = same ? (const __nv_bfloat16*)sa.p : (const __nv_bfloat16*)sb.p;
+    const CUtensorMap tmA = slice_map((const __nv_bfloat16*)sa.p, kpad, cols, OZ_BM, 1);
+    const CUtensorMap tmB = slice_map(SB, kpad, cols, OZ_BN, OZ_SLICES);
+    // rows per CTA: a multiple of OZ_CHUNK, at most OZ_MAX_RANGE, enough
+    // splits that the tiles x splits fill the SMs
+    const int tm = (cols + OZ_BM - 1) / OZ_BM, tn = (cols + OZ_BN - 1) / OZ_BN;
+    const int64_t chunks = (kpad + OZ_CHUNK - 1) / OZ_CHUNK;
+    int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(chunks, sms / std::max(1, tm * tn)));
+    int64_t range = (chunks + nsplit - 1) / nsplit * OZ_CHUNK;
+    if (range > OZ_MAX_RANGE) range = OZ_MAX_RANGE;
+    nsplit = (kpad + range - 1) / range;
+    OzBuf P((size_t)nsplit * cols * cols * sizeof(double), s);
+    const size_t smem = oz_gram_smem_bytes();
+    static bool attr = false;
+    if (!attr) {
+        CHEBFD_CHECK_CUDA(cudaFuncSetAttribute(oz_gram_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        attr = true;
+    }
+    const dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)nsplit);
+    oz_gram_kernel<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, range, kpad, cols, cols,
+                                                  (double*)P.p);
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+    const int total = m * m;
+    oz_finish_kernel<<<std::min(4096, (total + 255) / 256), 256, 0, s>>>(
+        (const double*)P.p, (int)nsplit, cols, m, cplx, (const int*)ea.p, eB, C, m);
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+}
+
+// CHEBFD_ETIMEOUT if an Ozaki Gram kernel gave up a bounded wait since the
+// last check (the flag is then cleared).  Synchronizes the stream.
+void check_oz_errors(cudaStream_t s) {
+    unsigned int h = 0;
+    CHEBFD_CHECK_CUDA(cudaMemcpyFromSymbolAsync(&h, g_oz_error, sizeof(h), 0,
+                                                cudaMemcpyDeviceToHost, s));
+    CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (h != 0) {
+        const unsigned int zero = 0;
+        CHEBFD_CHECK_CUDA(cudaMemcpyToSymbolAsync(g_oz_error, &zero, sizeof(zero), 0,
+                                                  cudaMemcpyHostToDevice, s));
+        CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+        CHEBFD_REQUIRE(false, CHEBFD_ETIMEOUT,
+                       "the tensor-core Gram gave up waiting for its pipeline stages");
+    }
+}
+
+}  // namespace chebfd

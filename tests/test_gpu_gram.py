@@ -1,0 +1,120 @@
+"""The tall Gram product of the orthonormalisation and Rayleigh-Ritz steps
+(Sec. 3.1 steps 6-7), A^H B for N x m blocks, by the three methods of
+chebfd_gram: cuBLAS FP64, the double-float kernel and the split onto the bf16
+tensor cores.  The reference is the plain definition: on small cases every
+entry is the exactly rounded dot product (error-free products by Dekker's
+split, summed by math.fsum); on large ones numpy's FP64 product, whose own
+error is bounded by the same relative scale."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1510_04895_gb300 as pkg
+from paper_1510_04895_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _two_prod(a, b):
+    p = a * b
+    c = 134217729.0
+    ah = a * c
+    ah = ah - (ah - a)
+    al = a - ah
+    bh = b * c
+    bh = bh - (bh - b)
+    bl = b - bh
+    return p, ((ah * bh - p) + ah * bl + al * bh) + al * bl
+
+
+def exact_gram(A, B):
+    """A^H B with every entry the correctly rounded sum of exact products."""
+    Ar, Ai = np.real(A), np.imag(A) if np.iscomplexobj(A) else np.zeros_like(A)
+    Br, Bi = np.real(B), np.imag(B) if np.iscomplexobj(B) else np.zeros_like(B)
+    m = A.shape[1]
+    G = np.zeros((m, m), np.complex128 if np.iscomplexobj(A) else np.float64)
+
+    def dot(x, y):
+        p, e = _two_prod(x, y)
+        return np.concatenate([p, e])
+
+    for p_ in range(m):
+        for q in range(m):
+            re = math.fsum(np.concatenate([dot(Ar[:, p_], Br[:, q]), dot(Ai[:, p_], Bi[:, q])]))
+            if np.iscomplexobj(A):
+                im = math.fsum(np.concatenate([dot(Ar[:, p_], Bi[:, q]), -dot(Ai[:, p_], Br[:, q])]))
+                G[p_, q] = re + 1j * im
+            else:
+                G[p_, q] = re
+    return G
+
+
+def scale_of(A, B):
+    """|A|^H |B| (entrywise moduli): the scale of a dot product's rounding error."""
+    return np.abs(A).T @ np.abs(B)
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+@pytest.mark.parametrize("n,m", [(1, 1), (63, 5), (64, 7), (513, 3), (1000, 12), (4097, 9)])
+def test_gram_small_against_exact_definition(cplx, n, m):
+    """Ragged N around the 64-row K-blocks and the 512-row exact chunks,
+    m from 1 to 12 (partial 128 x 64 tiles), A != B and A == B."""
+    A0 = workloads.random_block(n + m, n, m, cplx)
+    B0 = workloads.random_block(n + 2 * m, n, m, cplx)
+    A = torch.from_numpy(A0).to(DEV)
+    B = torch.from_numpy(B0).to(DEV)
+    for X0, Y0, X, Y in ((A0, B0, A, B), (A0, A0, A, A)):
+        ref = exact_gram(X0, Y0)
+        sc = scale_of(X0, Y0)
+        for method in ("tensor", "double_float", "fp64"):
+            G = pkg.chebfd_gram(X, None if Y is X else Y, method=method).cpu().numpy()
+            err = (np.abs(G - ref) / sc).max()
+            tol = {"tensor": 2.0 ** -52, "double_float": 2.0 ** -44, "fp64": 2.0 ** -52 * n}[method]
+            assert err <= tol, (method, err, tol)
+
+
+def test_gram_wide_column_scales_and_zero_columns():
+    """Columns scaled by 2^-300 .. 2^300 (each column's own power-of-two scale),
+    an all-zero column and subnormal entries: every entry to FP64 accuracy
+    relative to its own scale."""
+    n, m = 2000, 8
+    rs = np.random.default_rng(4)
+    A0 = rs.uniform(-1, 1, (n, m)) * np.ldexp(1.0, np.arange(m) * 85 - 300)[None, :]
+    B0 = rs.uniform(-1, 1, (n, m)) * np.ldexp(1.0, 290 - np.arange(m) * 83)[None, :]
+    A0[:, 3] = 0.0
+    B0[:7, 5] = 1e-310                      # subnormals among normal entries
+    ref = exact_gram(A0, B0)
+    sc = scale_of(A0, B0)
+    G = pkg.chebfd_gram(torch.from_numpy(A0).to(DEV), torch.from_numpy(B0).to(DEV),
+                        method="tensor").cpu().numpy()
+    assert np.all(G[3, :] == 0.0)
+    ok = sc > 0
+    assert (np.abs(G - ref)[ok] / sc[ok]).max() <= 2.0 ** -50
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+def test_gram_large_methods_agree(cplx):
+    """70001 x 128 (several row splits per tile, 137 chunks) and an
+    orthonormalised 131072 x 96 block (11 chunks per CTA): the tensor-core
+    Gram agrees with numpy's FP64 product and with cuBLAS within 1e-13 of
+    |A|^H |B|, and with cuBLAS within 2e-15 on the orthonormal block (whose
+    distance from the identity, ~3e-14 with some LAPACKs, belongs to the QR
+    factor, not to the product)."""
+    n, m = 70001, 128 if cplx else 200
+    A0 = workloads.random_block(31, n, m, cplx)
+    B0 = workloads.random_block(32, n, m, cplx)
+    A, B = torch.from_numpy(A0).to(DEV), torch.from_numpy(B0).to(DEV)
+    ref = A0.conj().T @ B0
+    sc = scale_of(A0, B0)
+    for method in ("tensor", "fp64"):
+        G = pkg.chebfd_gram(A, B, method=method).cpu().numpy()
+        assert (np.abs(G - ref) / sc).max() <= 1e-13, method
+    Q0 = np.linalg.qr(workloads.random_block(33, 131072, 96, cplx))[0]
+    Q = torch.from_numpy(np.ascontiguousarray(Q0)).to(DEV)
+    G = pkg.chebfd_gram(Q, method="tensor").cpu().numpy()
+    Gb = pkg.chebfd_gram(Q, method="fp64").cpu().numpy()
+    assert np.abs(G - Gb).max() <= 2e-15
+    assert np.abs(G - Q0.conj().T @ Q0).max() <= 2e-15 + 96 * 2.0 ** -53
