@@ -382,6 +382,21 @@ typedef enum chebfd_gram_method {
 chebfd_status chebfd_gram(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n,
                           int m, chebfd_dtype dt, double* C, int method, void* stream);
 
+/* The tall block update of the orthonormalisation and Rayleigh-Ritz steps
+ * (Sec. 3.1 steps 6-7: Y <- Y T and the Ritz vectors V = Y S):
+ * T[p][i] = sum_q Y[p][q] conj(M[q + i ldm]) for a device block Y (N x k, ldy,
+ * row-major) and a DEVICE k x r column-major M (ldm; for C128 interleaved
+ * complex), into the device block T (N x r, ldt), R64 or C128; T must not
+ * overlap Y.  (M holds the complex conjugate of the transform, the layout in
+ * which the Hermitian eigensolvers return column-major eigenvectors of the
+ * Gram matrices of chebfd_gram.)  Methods as for chebfd_gram; the tensor
+ * method splits every row of Y and every column of M into 8 bf16 digit
+ * slices and needs 16 N k (32 N k complex) bytes of workspace; k <= 131072.
+ * EINVAL on bad arguments; ETIMEOUT as for chebfd_gram.  Synchronizes. */
+chebfd_status chebfd_block_update(const void* Y, int64_t ldy, int64_t n, int k, const double* M,
+                                  int ldm, int r, void* T, int64_t ldt, chebfd_dtype dt,
+                                  int method, void* stream);
+
 /* Y = X with a change of precision (R64 <-> R32, C128 <-> C64, or a copy);
  * device blocks N x nb with leading dimensions ldx, ldy; round to nearest. */
 chebfd_status chebfd_convert_block(const void* X, chebfd_dtype xdt, int64_t ldx, void* Y,
@@ -516,11 +531,31 @@ typedef enum chebfd_precision {
 
 /* Bits of chebfd_params.flags. */
 typedef enum chebfd_solve_flags {
-    CHEBFD_SOLVE_HARMONIC = 1 /* step 7 with harmonic Ritz pairs for the target
+    CHEBFD_SOLVE_HARMONIC = 1, /* step 7 with harmonic Ritz pairs for the target
                                  tau = (lam_lo + lam_hi)/2 (chebfd_harmonic_ritz):
                                  window test, ghosts and convergence use their
                                  Rayleigh quotients and residuals; the restart
                                  block is the set of harmonic vectors */
+    CHEBFD_SOLVE_LOCKING = 4,  /* hard locking of converged pairs (Sec. 6): an
+                                 accepted in-window pair with residual <= eps ||H||
+                                 leaves the search block (four at a time, the
+                                 smallest residuals first, at least four columns
+                                 stay) and is kept as found; every later filtered
+                                 block is deflated against the locked vectors
+                                 (twice) and the search block shrinks; EINVAL
+                                 together with CHEBFD_SOLVE_HARMONIC */
+    CHEBFD_SOLVE_ADAPTIVE = 2  /* adaptive degree (Sec. 6 with the rule of Sec. 2.4):
+                                 the first filter also returns its Chebyshev
+                                 moments; averaged over the n_s random search
+                                 vectors (normalised by <x_k, x_k>) they are a
+                                 stochastic-trace KPM estimate of the DOS, from
+                                 which N_T (Eq. DOS:target), the margin delta'
+                                 where the search interval holds n_s states
+                                 (Eq. DOS:search) and N_p = N_0 S_w / delta'
+                                 (N_0 of Tab. lanczoskernel at the window
+                                 centre) follow; that N_p, within [Np/4, 4 Np]
+                                 of the given one, is used from the second
+                                 iteration on (per-iteration records show it) */
 } chebfd_solve_flags;
 
 /* Parameters of chebfd_solve.  Zero / negative fields take the defaults given. */
@@ -583,7 +618,7 @@ typedef struct chebfd_result_info {
     int32_t iterations;
     int32_t converged;
     int32_t fp64_iterations;    /* iterations whose filter ran in FP64 (double-float in MIXED_DF) */
-    int64_t n_mvm;              /* N_iter * N_S * N_p products with H (vector count) */
+    int64_t n_mvm;              /* products with H (vector count): sum over iterations of N_S N_p */
     double a, b;                /* spectral interval used */
     double seconds_filter, seconds_dense, seconds_total;
     const double* lambda;
@@ -609,6 +644,8 @@ typedef struct chebfd_iteration_info {
     int32_t ghosts;             /* of them ghost-flagged */
     int32_t accepted;           /* in-window pairs accepted (not ghosts) */
     int32_t converged_pairs;    /* accepted pairs with residual <= eps ||H|| */
+    int32_t Np;                 /* degree of this iteration's filter */
+    int32_t locked;             /* pairs locked before this iteration (CHEBFD_SOLVE_LOCKING) */
     double res_min, res_max;    /* over the accepted pairs, absolute; -1 when none */
     double seconds_filter;      /* host wall time of the filter (stream synchronized) */
     double seconds_dense;       /* host wall time of steps 6-7 */

@@ -45,6 +45,17 @@ def chebyshev_vectors(H, alpha, beta, X, nmax):
 
 
 def moments(H, alpha, beta, X, count):
-    """mu_n[k] = Re <x_k, T_n(A) x_k>, n = 0..count-1 (Sec. 4): array count x n_b."""
-    T = chebyshev_vectors(H, alpha, beta, X, count - 1)
-    return np.array([np.real(np.sum(np.conj(X) * Tn, axis=0)) for Tn in T])
+    """mu_n[k] = Re <x_k, T_n(A) x_k>, n = 0..count-1 (Sec. 4): array count x n_b.
+    T_n(A) X from the recurrence, keeping only the two latest blocks."""
+    X = np.asarray(X)
+    out = np.zeros((count, X.shape[1]))
+    t_prev, t_cur = None, np.array(X, copy=True)
+    for n in range(count):
+        out[n] = np.real(np.sum(np.conj(X) * t_cur, axis=0))
+        if n + 1 == count:
+            break
+        if n == 0:
+            t_prev, t_cur = t_cur, apply_A(H, alpha, beta, X)
+        else:
+            t_prev, t_cur = t_cur, 2.0 * apply_A(H, alpha, beta, t_cur) - t_prev
+    return out

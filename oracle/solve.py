@@ -30,11 +30,62 @@ Readings of the paper taken here (the paper leaves them open):
   membership, ghosts and convergence then use their Rayleigh quotients and
   residuals, and the restart block is the set of harmonic vectors;
 * search vectors (step 4): SplitMix64 stream 1, column k of n_s, entry 2u-1 at
-  word index i*n_s + k (real) or 2(i*n_s + k) + {0, 1} (complex parts).
+  word index i*n_s + k (real) or 2(i*n_s + k) + {0, 1} (complex parts);
+* locking=True (hard locking of converged pairs, named in Sec. 6): an accepted
+  in-window pair whose residual is <= eps ||H|| leaves the search block and
+  is kept as found; later filtered blocks are deflated against the locked
+  vectors (Y <- Y - L L^H Y, twice) before SVQB, and the search block
+  shrinks to n_s minus the locked count.  Pairs are locked four at a time
+  (the smallest residuals first; the filter kernels take panel widths in
+  multiples of 16 bytes), the rest stay in the block.  Convergence is the
+  rule above with the locked pairs counted as accepted and converged;
+* adaptive=True (the adaptive choice of N_p that Sec. 6 suggests, with the
+  rule of Sec. 2.4): the random start block is a set of n_s stochastic-trace
+  probes, so the Chebyshev moments of the first filter (Sec. 4),
+  <x_k, T_n(A) x_k> / <x_k, x_k> averaged over the columns, estimate the
+  DOS (the KPM of Sec. 3.1 step 1 without extra products).  From them: the
+  target count N_T (Eq. DOS:target), the margin delta' at which the count
+  of the search interval reaches n_s (Eq. DOS:search), and
+  N_p = N_0 S_w / delta' (Sec. 2.4, N_0 of Tab. lanczoskernel at the window
+  centre), kept within [N_p / 4, 4 N_p] of the first degree, for every later
+  iteration.
 """
 import numpy as np
 
-from . import coeffs, filter as filt, rng, rr, svqb
+from . import coeffs, filter as filt, kpm, rng, rr, svqb
+
+# N_0 of the Lanczos kernel (mu = 2) at the interval centre c / S_w = 0, 0.1,
+# .., 0.9 (Tab. lanczoskernel), linearly interpolated, the last value beyond.
+TAB_LANCZOS_N0 = (6.23, 6.20, 6.10, 5.94, 5.71, 5.40, 4.99, 4.46, 3.75, 2.73)
+
+
+def lanczos_N0(rel_centre):
+    x = min(abs(rel_centre), 0.9) * 10.0
+    i = min(int(x), 8)
+    f = x - i
+    return TAB_LANCZOS_N0[i] * (1.0 - f) + TAB_LANCZOS_N0[i + 1] * f
+
+
+def degree_from_moments(mu, D, a, b, lam_lo, lam_hi, ns, Np0, M_max=1024):
+    """(N_T, delta', N_p) from normalised moments mu (Sec. 2.4, Sec. 3.1 steps 2-3):
+    the KPM count in the window, the margin where the count of the search
+    interval reaches n_s (bisection), N_p = N_0 S_w / delta' within
+    [N_p0 / 4, 4 N_p0]."""
+    mu = np.asarray(mu[:M_max], dtype=np.float64)
+    NT = max(0.0, kpm.count_in_window(mu, D, a, b, lam_lo, lam_hi))
+    d_lo, d_hi = 0.0, b - a
+    for _ in range(60):
+        d = 0.5 * (d_lo + d_hi)
+        lo, hi = max(a, lam_lo - d), min(b, lam_hi + d)
+        if kpm.count_in_window(mu, D, a, b, lo, hi) < ns:
+            d_lo = d
+        else:
+            d_hi = d
+    dprime = max(0.5 * (d_lo + d_hi), 1e-12)
+    S_w = 0.5 * (b - a)
+    centre = 0.5 * (lam_lo + lam_hi) - 0.5 * (a + b)
+    Np = int(round(lanczos_N0(centre / S_w) * S_w / dprime))
+    return NT, dprime, int(min(max(Np, max(2, Np0 // 4)), 4 * Np0))
 
 
 def search_vectors(seed, D, ns, complex_values):
@@ -48,7 +99,7 @@ def search_vectors(seed, D, ns, complex_values):
 
 def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
            max_iter=40, filter_fn=None, X0=None, complex_values=None, extraction="ritz",
-           window_inset=0.0):
+           window_inset=0.0, adaptive=False, locking=False):
     """Run ChebFD; returns a dict with the accepted pairs and the iteration log.
 
     ``filter_fn(X)``, when given, replaces the recurrence of Fig. ChebFD by
@@ -68,9 +119,26 @@ def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
     prev = None
     prev_empty = False
     result = None
+    n_mvm = 0
+    adapted = None
+    L = np.zeros((D, 0), dtype=X.dtype)        # locked vectors and their pairs
+    lam_L, res_L = np.zeros(0), np.zeros(0)
     for it in range(1, max_iter + 1):
+        if adaptive and it == 1:
+            m = filt.moments(H, alpha, beta, X, 2 * Np)
+            adapted = degree_from_moments(np.mean(m / m[0][None, :], axis=1), D, a, b, lam_lo,
+                                          lam_hi, ns, Np)
         Y = filter_fn(X) if filter_fn is not None else filt.filter_block(H, alpha, beta, gc, X)
+        n_mvm += X.shape[1] * (len(gc) - 1)
+        if adaptive and it == 1:
+            gc = coeffs.filter_coeffs(a, b, c - d, c + d, adapted[2], kind, mu)
+        for _ in range(2 if L.shape[1] else 0):
+            Y = Y - L @ (L.conj().T @ Y)
         Q, rank, refill = svqb.svqb(Y, seed=seed, refill_counter=refill)
+        if L.shape[1]:
+            # refilled columns are random: deflate once more and re-orthonormalise
+            Q = Q - L @ (L.conj().T @ Q)
+            Q, _, refill = svqb.svqb(Q, seed=seed, refill_counter=refill)
         if extraction == "harmonic":
             theta, V, res, _ = rr.harmonic_ritz(H, Q, 0.5 * (lam_lo + lam_hi))
         else:
@@ -86,8 +154,8 @@ def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
                     ghost[k] = True
                 falling[k] = res[k] <= 0.9 * pres[j]
         acc = inwin & ~ghost
-        converged = bool(acc.any()) and bool(np.all(res[acc] <= eps * normH))
-        empty_now = prev is not None and not (acc | (inwin & falling)).any()
+        converged = (bool(acc.any()) or len(lam_L) > 0) and bool(np.all(res[acc] <= eps * normH))
+        empty_now = prev is not None and not (acc | (inwin & falling)).any() and not len(lam_L)
         if empty_now and prev_empty:
             converged = True
         prev_empty = empty_now
@@ -95,10 +163,23 @@ def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
                         ghosts=int(ghost.sum()), accepted=int(acc.sum()),
                         res_min=float(res[acc].min()) if acc.any() else None,
                         res_max=float(res[acc].max()) if acc.any() else None))
-        result = dict(theta=theta[acc], V=V[:, acc], res=res[acc], iterations=it,
-                      n_mvm=it * ns * Np, converged=converged, log=log, normH=normH)
+        result = dict(theta=np.concatenate([lam_L, theta[acc]]),
+                      V=np.concatenate([L, V[:, acc]], axis=1),
+                      res=np.concatenate([res_L, res[acc]]), iterations=it,
+                      n_mvm=n_mvm, converged=converged, log=log, normH=normH,
+                      Np=len(gc) - 1, adapted=adapted, locked=len(lam_L))
         if converged:
             break
-        prev = (theta, res)
-        X = V
+        keep = np.ones(len(theta), dtype=bool)
+        if locking:
+            done = np.nonzero(acc & (res <= eps * normH))[0]
+            done = done[np.argsort(res[done], kind="stable")]
+            done = np.sort(done[:len(done) // 4 * 4])
+            if len(done) and len(theta) - len(done) >= 4:
+                L = np.concatenate([L, V[:, done]], axis=1)
+                lam_L = np.concatenate([lam_L, theta[done]])
+                res_L = np.concatenate([res_L, res[done]])
+                keep[done] = False
+        prev = (theta[keep], res[keep])
+        X = V[:, keep]
     return result

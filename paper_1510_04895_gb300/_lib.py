@@ -102,6 +102,9 @@ SIGNATURES = {
     "chebfd_result_iterations": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int, c_i32p]),
     "chebfd_gram": (ctypes.c_int, [c_vp, ctypes.c_int64, c_vp, ctypes.c_int64, ctypes.c_int64,
                                    ctypes.c_int, ctypes.c_int, c_vp, ctypes.c_int, c_vp]),
+    "chebfd_block_update": (ctypes.c_int, [c_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                           c_vp, ctypes.c_int, ctypes.c_int, c_vp,
+                                           ctypes.c_int64, ctypes.c_int, ctypes.c_int, c_vp]),
     "chebfd_ensemble_create": (ctypes.c_int, [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_int,
                                               c_vp, ctypes.POINTER(c_vp)]),
     "chebfd_ensemble_info": (ctypes.c_int, [c_vp, c_i64p, c_i32p, c_i64p, c_i32p, c_i32p,
@@ -162,6 +165,7 @@ class IterationInfo(ctypes.Structure):
     _fields_ = [("iteration", ctypes.c_int32), ("fp64_filter", ctypes.c_int32),
                 ("in_window", ctypes.c_int32), ("ghosts", ctypes.c_int32),
                 ("accepted", ctypes.c_int32), ("converged_pairs", ctypes.c_int32),
+                ("Np", ctypes.c_int32), ("locked", ctypes.c_int32),
                 ("res_min", ctypes.c_double), ("res_max", ctypes.c_double),
                 ("seconds_filter", ctypes.c_double), ("seconds_dense", ctypes.c_double),
                 ("seconds_gram", ctypes.c_double), ("seconds_block_gemm", ctypes.c_double),
@@ -379,7 +383,26 @@ def chebfd_gram(A, B=None, method="tensor", stream=None):
                              _ptr(C), GRAM_METHODS[method], _stream(stream)), "chebfd_gram")
     # the library stores C[p + q m] = sum_i A[i,p] conj(B[i,q]) column-major: read
     # row-major that is C_rm[q, p]; A^H B [p, q] = conj(C_rm[q, p])
-    return C.T.conj()
+    return torch.conj_physical(C.T) if C.is_complex() else C.T
+
+
+def chebfd_block_update(Y, M, method="tensor", stream=None):
+    """Y @ M for a device block Y (N x k) and a device k x r matrix M (R64/C128):
+    the tall block update of steps 6-7 by cuBLAS FP64 ("fp64"), the
+    double-float kernel ("double_float") or the bf16 tensor-core split
+    ("tensor").  Returns a new N x r device tensor."""
+    import torch
+    n, k = Y.shape[0], Y.shape[1]
+    r = M.shape[1]
+    assert M.shape[0] == k and M.dtype == Y.dtype
+    # the library takes conj(M) column-major: that is M^H stored row-major
+    # (conj_physical: a lazy conj() would hand the library unconjugated memory)
+    Mc = torch.conj_physical(M).T.contiguous() if M.is_complex() else M.T.contiguous()
+    T = torch.empty((n, r), dtype=Y.dtype, device=Y.device)
+    _check(lib().chebfd_block_update(_ptr(Y), Y.stride(0), n, k, _ptr(Mc), k, r, _ptr(T),
+                                     T.stride(0), dtype_of(Y), GRAM_METHODS[method],
+                                     _stream(stream)), "chebfd_block_update")
+    return T
 
 
 def chebfd_chebyshev_step(H, alpha, beta, c, U, W, Y, stream=None):
@@ -454,15 +477,19 @@ EXTRACTION = {"ritz": 0, "harmonic": 1}
 
 def chebfd_solve(H, lam_lo, lam_hi, ns, Np, eps=1e-9, kernel="lanczos", mu=2.0, nb=0,
                  precision="fp64", max_iter=50, seed=0, a=0.0, b=0.0, lanczos_steps=30,
-                 stream=None, extraction="ritz", window_inset=0.0):
+                 stream=None, extraction="ritz", window_inset=0.0, adaptive=False,
+                 locking=False):
     """Run ChebFD; returns a dict with lambda, res (numpy), V (torch, device) and the log.
     extraction="harmonic" uses harmonic Ritz pairs for the window centre;
-    window_inset=f filters with the window narrowed by f of the half-width."""
+    window_inset=f filters with the window narrowed by f of the half-width;
+    adaptive=True sets N_p from the first filter's moments (the log shows it);
+    locking=True locks converged pairs out of the search block."""
     p = Params(lam_lo=lam_lo, lam_hi=lam_hi, eps=eps, a=a, b=b, mu=mu, ns=ns, Np=Np,
                kernel=KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel), nb=nb,
                precision=PRECISION[precision], max_iter=max_iter,
-               lanczos_steps=lanczos_steps, flags=EXTRACTION[extraction], seed=seed,
-               window_inset=window_inset)
+               lanczos_steps=lanczos_steps,
+               flags=EXTRACTION[extraction] | (2 if adaptive else 0) | (4 if locking else 0),
+               seed=seed, window_inset=window_inset)
     h = c_vp()
     st = lib().chebfd_solve(H.handle, ctypes.byref(p), _stream(stream), ctypes.byref(h))
     if st not in (0, 5) or not h:

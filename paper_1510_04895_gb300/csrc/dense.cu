@@ -31,6 +31,10 @@ void df_gemm(bool cplx, int r, int64_t n, int k, const double* Mt, int ldm, cons
 void oz_gram(bool cplx, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n,
              int m, double* C, int sms, cudaStream_t s);
 void check_oz_errors(cudaStream_t s);
+void oz_gemm(bool cplx, int r, int64_t n, int k, const double* M, int ldm, const double* Y,
+             int64_t ldy, double* T, int64_t ldt, int sms, cudaStream_t s, bool conj);
+void oz_gram_rect(bool cplx, const double* A, int64_t lda, int ma, const double* B, int64_t ldb,
+                  int mb, int64_t n, double* C, int sms, cudaStream_t s);
 
 namespace {
 
@@ -389,6 +393,83 @@ void residuals_from_blocks(bool cplx, const double* HV, const double* V, const d
     CHEBFD_CHECK_CUDA(cudaGetLastError());
 }
 
+namespace {
+
+// Y[i][k] -= T[i][k] for k < w doubles per row (Y: ld, T: ldt doubles per row).
+__global__ void sub_block_kernel(double* __restrict__ Y, int64_t ld, const double* __restrict__ T,
+                                 int64_t ldt, int64_t n, int w) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * w;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / w;
+        const int k = (int)(t - i * w);
+        Y[i * ld + k] -= T[i * ldt + k];
+    }
+}
+
+// dst[i][j] = src[i][idx[j]] (entries of ew doubles), j < cnt.
+__global__ void gather_columns_kernel(const double* __restrict__ src, int64_t ld, int64_t n,
+                                      const int* __restrict__ idx, int cnt, int ew,
+                                      double* __restrict__ dst, int64_t ldd) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * cnt;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / cnt;
+        const int j = (int)(t - i * cnt);
+        for (int e = 0; e < ew; ++e) dst[(i * ldd + j) * ew + e] = src[(i * ld + idx[j]) * ew + e];
+    }
+}
+
+}  // namespace
+
+// Y (N x w, ld) <- Y - L (L^H Y), twice, for the locked vectors L (N x nl,
+// ld): the rectangular Gram and block product on the tensor cores (tensor)
+// or with cuBLAS FP64.  Hard locking of converged pairs (Sec. 6).
+void deflate_impl(bool cplx, const double* L, int nl, double* Y, int w, int64_t n, int64_t ld,
+                  bool tensor, int sms, cudaStream_t s) {
+    if (nl <= 0 || w <= 0) return;
+    const size_t es = cplx ? 16 : 8;
+    Buf C((size_t)nl * w * es, s), T((size_t)n * w * es, s);
+    Handles& h = handles_for_current_device(s);
+    for (int pass = 0; pass < 2; ++pass) {
+        // C[p + q nl] = sum_i L[i,p] conj(Y[i,q]);  T = L conj(C) = L (L^H Y)
+        if (tensor) {
+            oz_gram_rect(cplx, L, ld, nl, Y, ld, w, n, C.as<double>(), sms, s);
+            oz_gemm(cplx, w, n, nl, C.as<double>(), nl, L, ld, T.as<double>(), w, sms, s, true);
+        } else {
+            if (cplx) {
+                const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0),
+                                      zero = make_cuDoubleComplex(0.0, 0.0);
+                CHEBFD_CHECK_CUBLAS(cublasZgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_C, nl, w, (int)n,
+                                                &one, (const cuDoubleComplex*)L, (int)ld,
+                                                (const cuDoubleComplex*)Y, (int)ld, &zero,
+                                                C.as<cuDoubleComplex>(), nl));
+            } else {
+                const double one = 1.0, zero = 0.0;
+                CHEBFD_CHECK_CUBLAS(cublasDgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_T, nl, w, (int)n,
+                                                &one, L, (int)ld, Y, (int)ld, &zero,
+                                                C.as<double>(), nl));
+            }
+            gemm_ch(h, cplx, w, n, nl, C.as<double>(), nl, L, ld, T.as<double>(), w);
+        }
+        const int ew = cplx ? 2 : 1;
+        sub_block_kernel<<<grid1d(n * w * ew), 256, 0, s>>>(Y, ld * ew, T.as<double>(), (int64_t)w * ew,
+                                                            n, w * ew);
+        CHEBFD_CHECK_CUDA(cudaGetLastError());
+    }
+}
+
+// dst[i][j] = src[i][idx[j]] for FP64 blocks (complex: 2 doubles per entry).
+void gather_columns_impl(const double* src, int64_t ld, int64_t n, const std::vector<int>& idx,
+                         bool cplx, double* dst, int64_t ldd, cudaStream_t s) {
+    if (idx.empty()) return;
+    Buf d((size_t)idx.size() * sizeof(int), s);
+    CHEBFD_CHECK_CUDA(cudaMemcpyAsync(d.p, idx.data(), idx.size() * sizeof(int),
+                                      cudaMemcpyHostToDevice, s));
+    gather_columns_kernel<<<grid1d(n * (int64_t)idx.size()), 256, 0, s>>>(
+        src, ld, n, d.as<int>(), (int)idx.size(), cplx ? 2 : 1, dst, ldd);
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+    CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));   // idx buffer freed after the copy
+}
+
 void orthonormalize_impl(void* Yv, int64_t n, int ns, int64_t ld, chebfd_dtype dt,
                          uint64_t seed, int64_t* refill_counter, int* rank_out, cudaStream_t s) {
     check_fp64_block(dt, Yv, n, ns, ld);
@@ -658,9 +739,8 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
         T((size_t)n * ld * es, s);
     std::vector<double> hth(ns);
     int64_t counter = refill_counter ? *refill_counter : 0;
-    // tall products: cuBLAS FP64, or (df) the Grams on the bf16 tensor cores
-    // (FP64-accurate split, oz_gram.cu) and the block products as
-    // double-float kernels
+    // tall products: cuBLAS FP64, or (df) the bf16 tensor cores with the
+    // FP64-accurate split of oz_gram.cu
     auto tall_gram = [&](const double* A, const double* B, double* C) {
         if (df)
             oz_gram(cplx, A, ld, B, ld, n, ns, C, M.num_sms, s);
@@ -669,7 +749,7 @@ void ortho_rr_impl(const Matrix& M, void* Yv, int64_t ld, int ns, chebfd_dtype d
     };
     auto tall_gemm = [&](int r, const double* Mc, const double* Yb, double* Tb) {
         if (df)
-            df_gemm(cplx, r, n, ns, Mc, ns, Yb, ld, Tb, ld, s);
+            oz_gemm(cplx, r, n, ns, Mc, ns, Yb, ld, Tb, ld, M.num_sms, s, true);
         else
             gemm_ch(h, cplx, r, n, ns, Mc, ns, Yb, ld, Tb, ld);
     };
@@ -861,6 +941,43 @@ extern "C" chebfd_status chebfd_gram(const void* A, int64_t lda, const void* B, 
                 break;
             default:
                 CHEBFD_REQUIRE(false, CHEBFD_EINVAL, "unknown Gram method");
+        }
+        CHEBFD_CHECK_CUDA(cudaGetLastError());
+        check_oz_errors(s);
+    });
+}
+
+extern "C" chebfd_status chebfd_block_update(const void* Y, int64_t ldy, int64_t n, int k,
+                                             const double* M, int ldm, int r, void* T,
+                                             int64_t ldt, chebfd_dtype dt, int method,
+                                             void* stream) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(Y && M && T && Y != T, CHEBFD_EINVAL, "null or overlapping argument");
+        CHEBFD_REQUIRE(dt == CHEBFD_R64 || dt == CHEBFD_C128, CHEBFD_EINVAL,
+                       "the block update takes FP64 blocks (R64 or C128)");
+        CHEBFD_REQUIRE(n >= 1 && k >= 1 && r >= 1 && ldy >= k && ldt >= r && ldm >= k,
+                       CHEBFD_EINVAL, "need n, k, r >= 1, ldy >= k, ldt >= r, ldm >= k");
+        CHEBFD_REQUIRE(n < (1LL << 31), CHEBFD_EINVAL, "N must be < 2^31");
+        const bool cplx = dt == CHEBFD_C128;
+        cudaStream_t s = as_stream(stream);
+        int dev = 0, sms = 0;
+        CHEBFD_CHECK_CUDA(cudaGetDevice(&dev));
+        CHEBFD_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        switch (method) {
+            case CHEBFD_GRAM_FP64: {
+                Handles& h = handles_for_current_device(s);
+                gemm_ch(h, cplx, r, n, k, M, ldm, (const double*)Y, ldy, (double*)T, ldt);
+                break;
+            }
+            case CHEBFD_GRAM_DOUBLE_FLOAT:
+                df_gemm(cplx, r, n, k, M, ldm, (const double*)Y, ldy, (double*)T, ldt, s);
+                break;
+            case CHEBFD_GRAM_TENSOR:
+                oz_gemm(cplx, r, n, k, M, ldm, (const double*)Y, ldy, (double*)T, ldt, sms, s,
+                        true);
+                break;
+            default:
+                CHEBFD_REQUIRE(false, CHEBFD_EINVAL, "unknown method");
         }
         CHEBFD_CHECK_CUDA(cudaGetLastError());
         check_oz_errors(s);

@@ -278,18 +278,29 @@ __device__ __forceinline__ bool oz_wait(OzSmem& sm, uint64_t* bar, uint32_t pari
     return false;
 }
 
-// One CTA: the 128 x 64 tile (m0, n0) of G over the rows [k_begin, k_end)
-// (k_begin a multiple of OZ_CHUNK); writes its part to P[split][m][n] in units
-// of one group-2 digit product.
+// Where a CTA's results go: without exponents, P[split][m][n] (ld = cols_b,
+// split stride cols_a * cols_b) in units of one group-2 digit product; with
+// the exponent fields ea[m], eb[n] (one split only), the finished values
+// 2^(ea - 1022 + eb - 1022 - 14) x that at out[m * ld + n].
+struct OzOut {
+    double* P;
+    int64_t ld;
+    const int* ea;
+    const int* eb;
+};
+
+// One CTA: the 128 x 64 tile (m0, n0) of D = A_s B_s^T over the rows
+// [k_begin, k_end) of the K dimension (k_begin a multiple of OZ_CHUNK), A_s
+// and B_s the digit slices (rows x K, K contiguous).
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   int64_t rows_per_split, int64_t kpad, int cols_a, int cols_b,
-                   double* __restrict__ P) {
+                   int64_t rows_per_split, int64_t kpad, int64_t cols_a, int cols_b, OzOut o) {
     extern __shared__ unsigned char smem_raw[];
     OzSmem& sm = *reinterpret_cast<OzSmem*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN, split = blockIdx.z;
+    const int64_t m0 = (int64_t)blockIdx.x * OZ_BM;
+    const int n0 = blockIdx.y * OZ_BN, split = blockIdx.z;
     const int64_t k_begin = split * rows_per_split;
     const int64_t k_end = min(kpad, k_begin + rows_per_split);
     const int nkb = (int)((k_end - k_begin) / OZ_BK);          // kpad is a multiple of OZ_BK
@@ -337,7 +348,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                         break;
                     }
                     mbar_arrive_expect_tx(&sm.a_full[as], A_TILE_BYTES);
-                    tma_load_3d(sm.a[as], &tmA, k, m0, i, &sm.a_full[as]);
+                    tma_load_3d(sm.a[as], &tmA, k, (int)m0, i, &sm.a_full[as]);
                     ++issued_a;
                 }
                 if (!ok) break;
@@ -432,15 +443,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             tmem_ld32(col_addr(OZ_EXACT), t7);
             tmem_ld32(col_addr(OZ_EXACT + 1), t8);
             tmem_ld32(col_addr(OZ_EXACT + 2), t9);
-            const int m = m0 + 32 * quarter + lane;
+            const int64_t m = m0 + 32 * quarter + lane;
             if (m < cols_a) {
-                double* out = P + ((size_t)split * cols_a + m) * cols_b;
+                double* out = o.P + ((size_t)split * cols_a + m) * o.ld;
+                const int em = o.ea ? (o.ea[m] > 0 ? o.ea[m] - 1022 : 0) - 14 : 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int n = n0 + 32 * half + j;
-                    if (n < cols_b)
-                        out[n] = ldexp((double)T[j], -28) + ldexp((double)t7[j], -35) +
-                                 ldexp((double)t8[j], -42) + ldexp((double)t9[j], -49);
+                    if (n < cols_b) {
+                        double v = ldexp((double)T[j], -28) + ldexp((double)t7[j], -35) +
+                                   ldexp((double)t8[j], -42) + ldexp((double)t9[j], -49);
+                        if (o.ea) v = ldexp(v, em + (o.eb[n] > 0 ? o.eb[n] - 1022 : 0));
+                        out[n] = v;
+                    }
                 }
             }
         }
@@ -451,19 +466,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
-// C (m x m, column-major, ldc) from the split partials: the fixed-order sum
+// C (ma x mb, column-major, ldc) from the split partials: the fixed-order sum
 // over splits, the column scales 2^(E_a - 1022) 2^(E_b - 1022) 2^-14, and for
 // complex blocks the combination of the four real parts of each entry:
 //     C[p + q ldc] = sum_i A[i,p] conj(B[i,q]).
-__global__ void oz_finish_kernel(const double* __restrict__ P, int nsplit, int cols, int m,
-                                 bool cplx, const int* ea, const int* eb, double* __restrict__ C,
-                                 int ldc) {
-    const int total = m * m;
+__global__ void oz_finish_kernel(const double* __restrict__ P, int nsplit, int ca, int cb,
+                                 int ma, int mb, bool cplx, const int* ea, const int* eb,
+                                 double* __restrict__ C, int ldc) {
+    const int total = ma * mb;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int p = t % m, q = t / m;
+        const int p = t % ma, q = t / ma;
         auto g = [&](int r, int c) {
             double s = 0.0;
-            for (int k = 0; k < nsplit; ++k) s += P[((size_t)k * cols + r) * cols + c];
+            for (int k = 0; k < nsplit; ++k) s += P[((size_t)k * ca + r) * cb + c];
             const int e = (ea[r] > 0 ? ea[r] - 1022 : 0) + (eb[c] > 0 ? eb[c] - 1022 : 0) - 14;
             return ldexp(s, e);
         };
@@ -505,7 +520,7 @@ EncodeTiledFn encode_tiled() {
 // Tensor map of the digit slices S[8][cols][kpad] (bf16): box of OZ_BK rows x
 // `rows` columns x `slices` slices, 128-byte swizzle (the layout the MMA
 // descriptors expect), zero fill outside the block.
-CUtensorMap slice_map(const __nv_bfloat16* S, int64_t kpad, int cols, int rows, int slices) {
+CUtensorMap slice_map(const __nv_bfloat16* S, int64_t kpad, int64_t cols, int rows, int slices) {
     CUtensorMap m;
     const cuuint64_t dim[3] = {(cuuint64_t)kpad, (cuuint64_t)cols, (cuuint64_t)OZ_SLICES};
     const cuuint64_t stride[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)cols * kpad * 2};
@@ -546,40 +561,119 @@ void oz_prepare(const double* A, int64_t n, int cols, int64_t ldr, int64_t kpad,
     CHEBFD_CHECK_CUDA(cudaGetLastError());
 }
 
+// ------------------------------------------------------------ block products
+
+// e[r] = largest biased exponent field of row r (kreal entries, ldr doubles
+// apart between rows): one warp per row.
+__global__ void oz_rowexp_kernel(const double* __restrict__ A, int64_t rows, int kreal,
+                                 int64_t ldr, int* __restrict__ e) {
+    const int lane = threadIdx.x % 32;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+    for (int64_t r = w0; r < rows; r += nw) {
+        const unsigned long long* row = reinterpret_cast<const unsigned long long*>(A + r * ldr);
+        unsigned mx = 0;
+        for (int k = lane; k < kreal; k += 32) mx = max(mx, (unsigned)((__ldg(row + k) >> 52) & 0x7FF));
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) e[r] = (int)mx;
+    }
+}
+
+// S[s][r][k] (bf16, kpad per row) = digit s of A[r][k] with the row's scale;
+// zero for kreal <= k < kpad.  One thread per pair of entries (one 32-bit
+// word per slice): reads and writes run along the row.
+__global__ void oz_rowsplit_kernel(const double* __restrict__ A, int64_t rows, int kreal,
+                                   int64_t ldr, const int* __restrict__ e, int64_t kpad,
+                                   uint32_t* __restrict__ S) {
+    const int64_t words = kpad / 2, total = rows * words;
+    const size_t slice_stride = (size_t)rows * words;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / words, j = t - r * words;
+        const int E = e[r];
+        const int k = (int)(2 * j);
+        const double x0 = k < kreal ? __ldg(A + r * ldr + k) : 0.0;
+        const double x1 = k + 1 < kreal ? __ldg(A + r * ldr + k + 1) : 0.0;
+        float d0[OZ_SLICES], d1[OZ_SLICES];
+        oz_digits(x0, E, d0);
+        oz_digits(x1, E, d1);
+#pragma unroll
+        for (int s = 0; s < OZ_SLICES; ++s) {
+            const __nv_bfloat162 v = __floats2bfloat162_rn(d0[s], d1[s]);
+            S[s * slice_stride + t] = *reinterpret_cast<const uint32_t*>(&v);
+        }
+    }
+}
+
+// Rows of the right operand for T = Y W, W = conj(M) (conj) or M, M a k x r
+// column-major matrix (ldm): real B[i][q] = W(q, i); complex, on the
+// interleaved real views, B[2i][2q] = Re W, B[2i][2q+1] = -Im W,
+// B[2i+1][2q] = Im W, B[2i+1][2q+1] = Re W (row-major, kreal per row).
+__global__ void oz_build_b_kernel(const double* __restrict__ M, int ldm, int k, int r, bool cplx,
+                                  bool conj, double* __restrict__ Bh) {
+    const int total = k * r;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int q = t % k, i = t / k;
+        if (!cplx) {
+            Bh[(size_t)i * k + q] = M[q + (size_t)i * ldm];
+            continue;
+        }
+        const double re = M[2 * (q + (size_t)i * ldm)];
+        const double im = conj ? -M[2 * (q + (size_t)i * ldm) + 1] : M[2 * (q + (size_t)i * ldm) + 1];
+        const size_t kr = 2 * (size_t)k;
+        Bh[(2 * (size_t)i) * kr + 2 * q] = re;
+        Bh[(2 * (size_t)i) * kr + 2 * q + 1] = -im;
+        Bh[(2 * (size_t)i + 1) * kr + 2 * q] = im;
+        Bh[(2 * (size_t)i + 1) * kr + 2 * q + 1] = re;
+    }
+}
+
+void oz_prepare_rows(const double* A, int64_t rows, int kreal, int64_t ldr, int64_t kpad, int* e,
+                     __nv_bfloat16* S, int sms, cudaStream_t s) {
+    const int g = (int)std::min<int64_t>((int64_t)sms * 16, std::max<int64_t>(1, (rows + 7) / 8));
+    oz_rowexp_kernel<<<g, 256, 0, s>>>(A, rows, kreal, ldr, e);
+    const int64_t work = rows * (kpad / 2);
+    const int g2 = (int)std::min<int64_t>((int64_t)sms * 32, std::max<int64_t>(1, (work + 255) / 256));
+    oz_rowsplit_kernel<<<g2, 256, 0, s>>>(A, rows, kreal, ldr, e, kpad,
+                                          reinterpret_cast<uint32_t*>(S));
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+}
+
 }  // namespace
 
 size_t oz_gram_smem_bytes() { return sizeof(OzSmem) + 1024; }
 
-// C (m x m, column-major, ld m) = A^T conj(B) summed over the N rows, i.e.
-// C[p + q m] = sum_i A[i,p] conj(B[i,q]) for row-major N x m blocks A (lda) and
-// B (ldb), FP64 real or complex (interleaved); B == A is recognised and split
-// once.  Asynchronous on s; workspace from the stream-ordered allocator.
-void oz_gram(bool cplx, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n,
-             int m, double* C, int sms, cudaStream_t s) {
-    const int cols = cplx ? 2 * m : m;
+// C (ma x mb, column-major, ld ma) with C[p + q ma] = sum_i A[i,p] conj(B[i,q])
+// for row-major blocks A (N x ma, lda) and B (N x mb, ldb), FP64 real or
+// complex (interleaved); B == A (same shape) is recognised and split once.
+// Asynchronous on s; workspace from the stream-ordered allocator.
+void oz_gram_rect(bool cplx, const double* A, int64_t lda, int ma, const double* B, int64_t ldb,
+                  int mb, int64_t n, double* C, int sms, cudaStream_t s) {
+    const int ca = cplx ? 2 * ma : ma, cb = cplx ? 2 * mb : mb;
     const int64_t ldra = cplx ? 2 * lda : lda, ldrb = cplx ? 2 * ldb : ldb;
-    CHEBFD_REQUIRE(cols >= 1 && cols <= 2048, CHEBFD_EINVAL, "Ozaki Gram: at most 2048 real columns");
+    CHEBFD_REQUIRE(ca >= 1 && cb >= 1 && ca <= 2048 && cb <= 2048, CHEBFD_EINVAL,
+                   "Ozaki Gram: between 1 and 2048 real columns per operand");
     CHEBFD_REQUIRE(n >= 1, CHEBFD_EINVAL, "Ozaki Gram: empty block");
     const int64_t kpad = (n + OZ_BK - 1) / OZ_BK * OZ_BK;
-    const bool same = A == B && lda == ldb;
-    const size_t slice_bytes = (size_t)OZ_SLICES * cols * kpad * sizeof(__nv_bfloat16);
-    OzBuf ea((size_t)cols * sizeof(int), s), eb(same ? 0 : (size_t)cols * sizeof(int), s);
-    OzBuf sa(slice_bytes, s), sb(same ? 0 : slice_bytes, s);
-    oz_prepare(A, n, cols, ldra, kpad, (int*)ea.p, (__nv_bfloat16*)sa.p, sms, s);
-    if (!same) oz_prepare(B, n, cols, ldrb, kpad, (int*)eb.p, (__nv_bfloat16*)sb.p, sms, s);
+    const bool same = A == B && lda == ldb && ma == mb;
+    OzBuf ea((size_t)ca * sizeof(int), s), eb(same ? 0 : (size_t)cb * sizeof(int), s);
+    OzBuf sa((size_t)OZ_SLICES * ca * kpad * sizeof(__nv_bfloat16), s);
+    OzBuf sb(same ? 0 : (size_t)OZ_SLICES * cb * kpad * sizeof(__nv_bfloat16), s);
+    oz_prepare(A, n, ca, ldra, kpad, (int*)ea.p, (__nv_bfloat16*)sa.p, sms, s);
+    if (!same) oz_prepare(B, n, cb, ldrb, kpad, (int*)eb.p, (__nv_bfloat16*)sb.p, sms, s);
     const int* eB = same ? (const int*)ea.p : (const int*)eb.p;
     const __nv_bfloat16* SB = same ? (const __nv_bfloat16*)sa.p : (const __nv_bfloat16*)sb.p;
-    const CUtensorMap tmA = slice_map((const __nv_bfloat16*)sa.p, kpad, cols, OZ_BM, 1);
-    const CUtensorMap tmB = slice_map(SB, kpad, cols, OZ_BN, OZ_SLICES);
+    const CUtensorMap tmA = slice_map((const __nv_bfloat16*)sa.p, kpad, ca, OZ_BM, 1);
+    const CUtensorMap tmB = slice_map(SB, kpad, cb, OZ_BN, OZ_SLICES);
     // rows per CTA: a multiple of OZ_CHUNK, at most OZ_MAX_RANGE, enough
     // splits that the tiles x splits fill the SMs
-    const int tm = (cols + OZ_BM - 1) / OZ_BM, tn = (cols + OZ_BN - 1) / OZ_BN;
+    const int tm = (ca + OZ_BM - 1) / OZ_BM, tn = (cb + OZ_BN - 1) / OZ_BN;
     const int64_t chunks = (kpad + OZ_CHUNK - 1) / OZ_CHUNK;
     int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(chunks, sms / std::max(1, tm * tn)));
     int64_t range = (chunks + nsplit - 1) / nsplit * OZ_CHUNK;
     if (range > OZ_MAX_RANGE) range = OZ_MAX_RANGE;
     nsplit = (kpad + range - 1) / range;
-    OzBuf P((size_t)nsplit * cols * cols * sizeof(double), s);
+    OzBuf P((size_t)nsplit * ca * cb * sizeof(double), s);
     const size_t smem = oz_gram_smem_bytes();
     static bool attr = false;
     if (!attr) {
@@ -589,12 +683,58 @@ void oz_gram(bool cplx, const double* A, int64_t lda, const double* B, int64_t l
         attr = true;
     }
     const dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)nsplit);
-    oz_gram_kernel<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, range, kpad, cols, cols,
-                                                  (double*)P.p);
+    const OzOut o{(double*)P.p, cb, nullptr, nullptr};
+    oz_gram_kernel<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, range, kpad, ca, cb, o);
     CHEBFD_CHECK_CUDA(cudaGetLastError());
-    const int total = m * m;
+    const int total = ma * mb;
     oz_finish_kernel<<<std::min(4096, (total + 255) / 256), 256, 0, s>>>(
-        (const double*)P.p, (int)nsplit, cols, m, cplx, (const int*)ea.p, eB, C, m);
+        (const double*)P.p, (int)nsplit, ca, cb, ma, mb, cplx, (const int*)ea.p, eB, C, ma);
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+}
+
+// The square case: C (m x m, ld m) = sum_i A[i,p] conj(B[i,q]).
+void oz_gram(bool cplx, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t n,
+             int m, double* C, int sms, cudaStream_t s) {
+    oz_gram_rect(cplx, A, lda, m, B, ldb, m, n, C, sms, s);
+}
+
+// T[p][i] = sum_q Y[p][q] W(q, i), W = conj(M) if conj else M, for a row-major
+// N x k block Y (ldy) and a k x r column-major M (ldm), FP64 real or complex,
+// into T (N x r, ldt; must not overlap Y), at FP64 accuracy on the bf16 tensor
+// cores: the digit slices of Y (per-row scales) and of the rows of W^T (per
+// output column), K = k real or 2k (complex) in chunks of 512, no row split.
+// Asynchronous on s; workspace from the stream-ordered allocator.
+void oz_gemm(bool cplx, int r, int64_t n, int k, const double* M, int ldm, const double* Y,
+             int64_t ldy, double* T, int64_t ldt, int sms, cudaStream_t s, bool conj) {
+    CHEBFD_REQUIRE(n >= 1 && k >= 1 && r >= 1, CHEBFD_EINVAL, "Ozaki block product: empty operand");
+    CHEBFD_REQUIRE(n < (1LL << 31), CHEBFD_EINVAL, "Ozaki block product: N must be < 2^31");
+    const int kreal = cplx ? 2 * k : k, rows_b = cplx ? 2 * r : r;
+    const int64_t kpad = (kreal + OZ_BK - 1) / OZ_BK * OZ_BK;
+    const int64_t range = (kpad + OZ_CHUNK - 1) / OZ_CHUNK * OZ_CHUNK;
+    CHEBFD_REQUIRE(range <= OZ_MAX_RANGE, CHEBFD_EINVAL, "Ozaki block product: k too large");
+    OzBuf ea((size_t)n * sizeof(int), s), eb((size_t)rows_b * sizeof(int), s);
+    OzBuf sa((size_t)OZ_SLICES * n * kpad * sizeof(__nv_bfloat16), s);
+    OzBuf bh((size_t)rows_b * kreal * sizeof(double), s);
+    OzBuf sb((size_t)OZ_SLICES * rows_b * kpad * sizeof(__nv_bfloat16), s);
+    oz_prepare_rows(Y, n, kreal, cplx ? 2 * ldy : ldy, kpad, (int*)ea.p, (__nv_bfloat16*)sa.p, sms,
+                    s);
+    oz_build_b_kernel<<<std::min(1024, (k * r + 255) / 256), 256, 0, s>>>(M, ldm, k, r, cplx, conj,
+                                                                          (double*)bh.p);
+    oz_prepare_rows((const double*)bh.p, rows_b, kreal, kreal, kpad, (int*)eb.p,
+                    (__nv_bfloat16*)sb.p, sms, s);
+    const CUtensorMap tmA = slice_map((const __nv_bfloat16*)sa.p, kpad, n, OZ_BM, 1);
+    const CUtensorMap tmB = slice_map((const __nv_bfloat16*)sb.p, kpad, rows_b, OZ_BN, OZ_SLICES);
+    const size_t smem = oz_gram_smem_bytes();
+    static bool attr = false;
+    if (!attr) {
+        CHEBFD_CHECK_CUDA(cudaFuncSetAttribute(oz_gram_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        attr = true;
+    }
+    const dim3 grid((unsigned)((n + OZ_BM - 1) / OZ_BM), (unsigned)((rows_b + OZ_BN - 1) / OZ_BN), 1);
+    const OzOut o{T, cplx ? 2 * ldt : ldt, (const int*)ea.p, (const int*)eb.p};
+    oz_gram_kernel<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, range, kpad, n, rows_b, o);
     CHEBFD_CHECK_CUDA(cudaGetLastError());
 }
 

@@ -106,6 +106,32 @@ void heuristic(const Matrix& M, const Analysis& A, double lo, double hi, int* ns
 
 }  // namespace
 
+// Adaptive degree (the adaptive choice of N_p suggested in Sec. 6, with the
+// rule of Sec. 2.4): mu are the normalised moments the first filter returned
+// for the n_s random search vectors (a stochastic-trace KPM estimate, at
+// most 1024 used); N_T from the window count, delta' where the count of the
+// search interval reaches n_s, N_p = N_0 S_w / delta' within [Np0/4, 4 Np0].
+int adaptive_degree(const std::vector<double>& mu_in, int64_t N, double a, double b, double lo,
+                    double hi, int ns, int Np0, double* n_target, double* dprime_out) {
+    const std::vector<double> mu(mu_in.begin(),
+                                 mu_in.begin() + std::min<size_t>(mu_in.size(), kCountMoments));
+    if (n_target) *n_target = std::max(0.0, kpm_count(mu, N, a, b, lo, hi));
+    double d_lo = 0.0, d_hi = b - a;
+    for (int it = 0; it < 60; ++it) {
+        const double d = 0.5 * (d_lo + d_hi);
+        if (kpm_count(mu, N, a, b, lo - d, hi + d) < ns)
+            d_lo = d;
+        else
+            d_hi = d;
+    }
+    const double dprime = std::max(0.5 * (d_lo + d_hi), 1e-12);
+    if (dprime_out) *dprime_out = dprime;
+    const double S_w = 0.5 * (b - a);
+    const double centre = 0.5 * (lo + hi) - 0.5 * (a + b);
+    const double n_p = std::round(lanczos_N0(centre / S_w) * S_w / dprime);
+    return (int)std::min<double>(std::max<double>(n_p, std::max(2, Np0 / 4)), 4.0 * Np0);
+}
+
 void features_of(const Matrix& M, const Analysis& A, double lo, double hi, int m_feat,
                  double* f) {
     for (int n = 0; n < m_feat; ++n) f[n] = n < (int)A.mu.size() ? A.mu[n] : 0.0;

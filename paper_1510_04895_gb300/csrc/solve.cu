@@ -31,6 +31,12 @@ void convert_block_impl(const void* X, chebfd_dtype xdt, int64_t ldx, void* Y, c
 void launch_random_block(void* X, int64_t n, int64_t ld, int nb, int col0, int ns_total,
                          uint64_t seed, chebfd_dtype dt, cudaStream_t stream);
 int max_panel_width(chebfd_dtype dt);
+int adaptive_degree(const std::vector<double>& mu, int64_t N, double a, double b, double lo,
+                    double hi, int ns, int Np0, double* n_target, double* dprime);
+void deflate_impl(bool cplx, const double* L, int nl, double* Y, int w, int64_t n, int64_t ld,
+                  bool tensor, int sms, cudaStream_t s);
+void gather_columns_impl(const double* src, int64_t ld, int64_t n, const std::vector<int>& idx,
+                         bool cplx, double* dst, int64_t ldd, cudaStream_t s);
 
 }  // namespace chebfd
 
@@ -102,8 +108,14 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
     CHEBFD_REQUIRE(p.precision >= CHEBFD_PRECISION_FP64 &&
                        p.precision <= CHEBFD_PRECISION_MIXED_DF,
                    CHEBFD_EINVAL, "unknown precision");
-    CHEBFD_REQUIRE((p.flags & ~CHEBFD_SOLVE_HARMONIC) == 0, CHEBFD_EINVAL, "unknown solve flags");
+    CHEBFD_REQUIRE((p.flags & ~(CHEBFD_SOLVE_HARMONIC | CHEBFD_SOLVE_ADAPTIVE |
+                                CHEBFD_SOLVE_LOCKING)) == 0,
+                   CHEBFD_EINVAL, "unknown solve flags");
     const bool harmonic = (p.flags & CHEBFD_SOLVE_HARMONIC) != 0;
+    const bool adaptive = (p.flags & CHEBFD_SOLVE_ADAPTIVE) != 0;
+    const bool locking = (p.flags & CHEBFD_SOLVE_LOCKING) != 0;
+    CHEBFD_REQUIRE(!(locking && harmonic), CHEBFD_EINVAL,
+                   "locking needs orthonormal Ritz vectors: not with harmonic pairs");
     const double tau = 0.5 * (p.lam_lo + p.lam_hi);
     const bool df = p.precision == CHEBFD_PRECISION_MIXED_DF;
     const bool mixed = p.precision == CHEBFD_PRECISION_MIXED || df;
@@ -118,16 +130,27 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
     // filter window: the target interval, narrowed by window_inset of its half-width
     const double wc = 0.5 * (p.lam_lo + p.lam_hi),
                  wh = 0.5 * (p.lam_hi - p.lam_lo) * (1.0 - p.window_inset);
-    const std::vector<double> gc = coefficients(a, b, wc - wh, wc + wh, p.Np, p.kernel, p.mu);
+    std::vector<double> gc = coefficients(a, b, wc - wh, wc + wh, p.Np, p.kernel, p.mu);
+    int Np = p.Np;
+    int64_t n_mvm = 0;
     const int64_t n = M.n;
     const int ns = p.ns;
     const int64_t ld = ns;  // rows start on 16 bytes in every precision (ns % 4 == 0)
     DevMem Y64((size_t)n * ld * dtype_size(d64));
+    // locking: the locked vectors, and a second block for compacting the rest
+    DevMem Lk(locking ? (size_t)n * ld * dtype_size(d64) : 0);
+    DevMem Yb(locking ? (size_t)n * ld * dtype_size(d64) : 0);
+    double* Y = (double*)Y64.p;
+    double* Yalt = (double*)Yb.p;
+    std::vector<double> lam_L, res_L;
+    int nl = 0, nact = ns;
     DevMem X32(mixed ? (size_t)n * ld * dtype_size(d32) : 0);
-    CHEBFD_CHECK_CUDA(cudaMemsetAsync(Y64.p, 0, (size_t)n * ld * dtype_size(d64), s));
-    launch_random_block(Y64.p, n, ld, ns, 0, ns, p.seed, d64, s);
+    // moments of the first filter (adaptive degree): 2 Np x ns
+    DevMem mom(adaptive ? (size_t)2 * p.Np * ns * sizeof(double) : 0);
+    CHEBFD_CHECK_CUDA(cudaMemsetAsync(Y, 0, (size_t)n * ld * dtype_size(d64), s));
+    launch_random_block(Y, n, ld, ns, 0, ns, p.seed, d64, s);
     bool single_phase = mixed;
-    if (mixed) convert_block_impl(Y64.p, d64, ld, X32.p, d32, ld, n, ns, s);
+    if (mixed) convert_block_impl(Y, d64, ld, X32.p, d32, ld, n, ns, s);
 
     std::vector<double> theta(ns), res(ns), prev_theta, prev_res;
     int64_t refill = 0;
@@ -140,28 +163,53 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
     for (it = 1; it <= p.max_iter; ++it) {
         // ---- step 5: filter
         double t0 = now();
+        const bool with_moments = adaptive && it == 1;
+        double* mom_dev = with_moments ? (double*)mom.p : nullptr;
+        const int Np_it = Np;
         if (single_phase) {
-            filter_block_impl(M, alpha, beta, gc.data(), p.Np, X32.p, ld, ns, d32, nullptr, s, p.nb);
-            convert_block_impl(X32.p, d32, ld, Y64.p, d64, ld, n, ns, s);
+            filter_block_impl(M, alpha, beta, gc.data(), Np, X32.p, ld, nact, d32, mom_dev, s,
+                              p.nb);
+            convert_block_impl(X32.p, d32, ld, Y, d64, ld, n, nact, s);
         } else {
-            if (df)
-                filter_block_df_impl(M, alpha, beta, gc.data(), p.Np, Y64.p, ld, ns, s);
+            if (df && !with_moments)
+                filter_block_df_impl(M, alpha, beta, gc.data(), Np, Y, ld, nact, s);
             else
-                filter_block_impl(M, alpha, beta, gc.data(), p.Np, Y64.p, ld, ns, d64, nullptr,
-                                  s, p.nb);
+                filter_block_impl(M, alpha, beta, gc.data(), Np, Y, ld, nact, d64, mom_dev, s,
+                                  p.nb);
             ++fp64_its;
         }
+        // locking: the filtered block leaves the span of the locked vectors
+        if (nl > 0) deflate_impl(cplx, (const double*)Lk.p, nl, Y, nact, n, ld, df, M.num_sms, s);
         CHEBFD_CHECK_CUDA(cudaStreamSynchronize(s));
+        n_mvm += (int64_t)nact * Np;
+        if (with_moments) {
+            // the n_s random columns as KPM probes: <x_k, T_n x_k> / <x_k, x_k>, averaged
+            std::vector<double> h((size_t)2 * Np * ns), mu(2 * Np, 0.0);
+            CHEBFD_CHECK_CUDA(cudaMemcpy(h.data(), mom.p, h.size() * sizeof(double),
+                                         cudaMemcpyDeviceToHost));
+            for (int k = 0; k < ns; ++k)
+                for (int q = 0; q < 2 * Np; ++q) mu[q] += h[(size_t)q * ns + k] / h[k] / ns;
+            Np = adaptive_degree(mu, n, a, b, p.lam_lo, p.lam_hi, ns, Np, nullptr, nullptr);
+            gc = coefficients(a, b, wc - wh, wc + wh, Np, p.kernel, p.mu);
+        }
         double t1 = now();
         t_filter += t1 - t0;
         chebfd_iteration_info rec{};
         rec.iteration = it;
+        rec.Np = Np_it;
         rec.fp64_filter = single_phase ? 0 : 1;
         rec.seconds_filter = t1 - t0;
         // ---- steps 6-7: orthonormalise, Rayleigh-Ritz
         double phase[PH_COUNT] = {0, 0, 0, 0, 0, 0};
-        ortho_rr_impl(M, Y64.p, ld, ns, d64, p.seed, &refill, theta.data(), res.data(), df,
+        const int64_t refill_before = refill;
+        ortho_rr_impl(M, Y, ld, nact, d64, p.seed, &refill, theta.data(), res.data(), df,
                       harmonic, tau, s, phase);
+        if (nl > 0 && refill != refill_before) {
+            // refilled random columns: out of the locked span once more
+            deflate_impl(cplx, (const double*)Lk.p, nl, Y, nact, n, ld, df, M.num_sms, s);
+            orthonormalize_impl(Y, n, nact, ld, d64, p.seed, &refill, nullptr, s);
+            rayleigh_ritz_impl(M, Y, ld, nact, d64, theta.data(), res.data(), nullptr, s);
+        }
         rec.seconds_dense = now() - t1;
         t_dense += rec.seconds_dense;
         rec.seconds_gram = phase[PH_GRAM];
@@ -173,13 +221,13 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
         // ---- step 8: window membership, ghosts, convergence
         acc_idx.clear();
         int in_window = 0, live = 0;
-        for (int k = 0; k < ns; ++k) {
+        for (int k = 0; k < nact; ++k) {
             if (!(theta[k] >= p.lam_lo && theta[k] <= p.lam_hi)) continue;
             ++in_window;
             bool ghost = false, falling = false;
             if (!prev_theta.empty()) {
                 int j = 0;
-                for (int q = 1; q < ns; ++q)
+                for (int q = 1; q < (int)prev_theta.size(); ++q)
                     if (std::fabs(prev_theta[q] - theta[k]) < std::fabs(prev_theta[j] - theta[k]))
                         j = q;
                 ghost = res[k] > std::sqrt(p.eps) * normH && !(prev_res[j] >= 10.0 * res[k]);
@@ -199,13 +247,14 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
         rec.ghosts = in_window - rec.accepted;
         rec.res_min = best;
         rec.res_max = acc_idx.empty() ? -1.0 : worst;
+        rec.locked = nl;
         R->iterations.push_back(rec);
-        converged = !acc_idx.empty() && worst <= p.eps * normH;
+        converged = (!acc_idx.empty() || nl > 0) && worst <= p.eps * normH;
         // empty window: two successive iterations (from the second on) without
         // an in-window pair that is accepted or still converging (residual at
         // most 0.9 of the previous nearest pair's): the ghost-flagged pairs of a
         // weak filter keep converging, spurious in-window values stagnate
-        const bool empty_now = !prev_theta.empty() && live == 0;
+        const bool empty_now = !prev_theta.empty() && live == 0 && nl == 0;
         if (empty_now && prev_empty) {
             converged = true;
             break;
@@ -220,14 +269,69 @@ void solve_impl(const Matrix& M, const chebfd_params& p0, cudaStream_t s, chebfd
             single_phase = false;  // residuals stalled at the single-precision floor
         }
         prev_worst = worst;
-        prev_theta = theta;
-        prev_res = res;
-        if (single_phase) convert_block_impl(Y64.p, d64, ld, X32.p, d32, ld, n, ns, s);
+        // locking: converged accepted pairs, the smallest residuals first, four
+        // at a time, leave the block (at least four columns stay)
+        std::vector<int> keep;
+        if (locking) {
+            std::vector<int> done;
+            for (int k : acc_idx)
+                if (res[k] <= p.eps * normH) done.push_back(k);
+            std::stable_sort(done.begin(), done.end(),
+                             [&](int x, int y) { return res[x] < res[y]; });
+            done.resize(done.size() / 4 * 4);
+            if (!done.empty() && nact - (int)done.size() >= 4) {
+                std::sort(done.begin(), done.end());
+                const int ew = cplx ? 2 : 1;
+                gather_columns_impl(Y, ld, n, done, cplx, (double*)Lk.p + (size_t)nl * ew, ld, s);
+                for (int k : done) {
+                    lam_L.push_back(theta[k]);
+                    res_L.push_back(res[k]);
+                }
+                for (int k = 0, q = 0; k < nact; ++k) {
+                    if (q < (int)done.size() && done[q] == k)
+                        ++q;
+                    else
+                        keep.push_back(k);
+                }
+                gather_columns_impl(Y, ld, n, keep, cplx, Yalt, ld, s);
+                std::swap(Y, Yalt);
+                nl += (int)done.size();
+            }
+        }
+        if (keep.empty()) {
+            prev_theta.assign(theta.begin(), theta.begin() + nact);
+            prev_res.assign(res.begin(), res.begin() + nact);
+        } else {
+            prev_theta.clear();
+            prev_res.clear();
+            for (int k : keep) {
+                prev_theta.push_back(theta[k]);
+                prev_res.push_back(res[k]);
+            }
+            nact = (int)keep.size();
+        }
+        if (single_phase) convert_block_impl(Y, d64, ld, X32.p, d32, ld, n, nact, s);
     }
     if (it > p.max_iter) it = p.max_iter;
     // ---- collect the accepted pairs (ascending theta: already sorted)
-    fill_result(R, acc_idx, theta, res, Y64.p, n, ld, dtype_size(d64), it, converged, fp64_its,
-                (int64_t)it * ns * p.Np, a, b, s);
+    if (nl > 0) {
+        // the locked pairs and the accepted ones of the last iteration, ascending
+        const int ew = cplx ? 2 : 1;
+        gather_columns_impl(Y, ld, n, acc_idx, cplx, (double*)Lk.p + (size_t)nl * ew, ld, s);
+        for (int k : acc_idx) {
+            lam_L.push_back(theta[k]);
+            res_L.push_back(res[k]);
+        }
+        std::vector<int> order(lam_L.size());
+        for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return lam_L[x] < lam_L[y]; });
+        fill_result(R, order, lam_L, res_L, Lk.p, n, ld, dtype_size(d64), it, converged,
+                    fp64_its, n_mvm, a, b, s);
+    } else {
+        fill_result(R, acc_idx, theta, res, Y, n, ld, dtype_size(d64), it, converged, fp64_its,
+                    n_mvm, a, b, s);
+    }
     R->info.seconds_filter = t_filter;
     R->info.seconds_dense = t_dense;
     R->info.seconds_total = now() - t_start;

@@ -254,3 +254,67 @@ def test_solve_weak_filter_is_not_taken_for_an_empty_window():
     G = pkg.chebfd_matrix_create_csr(np.arange(601), np.arange(600), gap)
     r = pkg.chebfd_solve(G, -0.05, 0.05, 16, 60, eps=1e-9, a=-1.01, b=1.01, max_iter=20)
     assert r["converged"] and r["nev"] == 0 and r["iterations"] <= 12
+
+
+def test_solve_adaptive_degree_matches_oracle_rule():
+    """Adaptive N_p (Sec. 6 with the rule of Sec. 2.4) through the C ABI on the
+    oracle pin's linear-DOS diagonal (D = 4000, N_T = 100, N_S = 200, started at
+    N_p = 300): the degree chosen from the first filter's moments agrees with
+    the oracle's (same search vectors) within 2 %, later iterations use it, all
+    100 eigenvalues are found, with fewer products than at the fixed degree.
+    The smallest insulator (MIXED_DF, first filter in complex64) also finds
+    every dense window eigenvalue."""
+    import scipy.sparse as sp
+    D, NS = 4000, 200
+    delta = np.sqrt(100.0 / D)
+    lam = lattice.linear_dos_eigs(D)
+    H = pkg.chebfd_matrix_create_csr(np.arange(D + 1), np.arange(D), lam)
+    r = pkg.chebfd_solve(H, -delta, delta, NS, 300, eps=1e-10, a=-1.0, b=1.0, adaptive=True)
+    ro = osolve.chebfd(sp.diags(lam).tocsr(), -1.0, 1.0, -delta, delta, NS, 300, 1e-10,
+                       complex_values=False, adaptive=True)
+    Np = ro["adapted"][2]
+    assert r["log"][0]["Np"] == 300
+    assert all(abs(rec["Np"] - Np) <= 0.02 * Np for rec in r["log"][1:])
+    exact = np.sort(lam[np.abs(lam) <= delta])
+    assert r["converged"] and r["nev"] == len(exact) == 100
+    assert np.abs(np.sort(r["lam"]) - exact).max() <= 1e-10
+    fixed = pkg.chebfd_solve(H, -delta, delta, NS, 300, eps=1e-10, a=-1.0, b=1.0)
+    assert r["n_mvm"] < fixed["n_mvm"]
+    Ht = pkg.chebfd_matrix_create_lattice("topi", 8, 8, 8, t=1.0, m=1.0, W=0.5, seed=0,
+                                          also_single=True)
+    Ho = lattice.to_scipy(*lattice.topi_csr(8, 8, 8, t=1.0, m=1.0, W=0.5, seed=0))
+    r = pkg.chebfd_solve(Ht, -0.1, 0.1, 64, 400, eps=1e-9, kernel="lanczos",
+                         precision="mixed_df", adaptive=True)
+    ew, _ = _dense_window(Ho, -0.1, 0.1)
+    normH = max(abs(r["a"]), abs(r["b"]))
+    assert r["converged"] and r["nev"] == len(ew) > 0
+    assert np.abs(np.sort(r["lam"]) - ew).max() <= 1e-10 * normH
+    assert r["log"][1]["Np"] != 400
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_df"])
+def test_solve_locking_matches_oracle(precision):
+    """Hard locking (Sec. 6) through the C ABI on the oracle pin's linear-DOS
+    diagonal (D = 4000, N_T = 100, N_S = 200, N_p = 95): pairs are locked four
+    at a time, all 100 eigenvalues are found with orthonormal vectors, fewer
+    products are needed than without locking (FP64: deflation with cuBLAS;
+    MIXED_DF: on the tensor cores).  Harmonic pairs with locking: EINVAL."""
+    D, NS, Np = 4000, 200, 95
+    delta = np.sqrt(100.0 / D)
+    lam = lattice.linear_dos_eigs(D)
+    H = pkg.chebfd_matrix_create_csr(np.arange(D + 1), np.arange(D), lam, also_single=True)
+    r = pkg.chebfd_solve(H, -delta, delta, NS, Np, eps=1e-10, a=-1.0, b=1.0,
+                         precision=precision, locking=True)
+    plain = pkg.chebfd_solve(H, -delta, delta, NS, Np, eps=1e-10, a=-1.0, b=1.0,
+                             precision=precision)
+    exact = np.sort(lam[np.abs(lam) <= delta])
+    assert r["converged"] and r["nev"] == len(exact) == 100
+    assert np.abs(r["lam"] - exact).max() <= 1e-10
+    V = r["V"].cpu().numpy()
+    assert np.abs(V.T @ V - np.eye(100)).max() <= 1e-10
+    locked = max(rec["locked"] for rec in r["log"])
+    assert locked >= 4 and locked % 4 == 0
+    assert r["n_mvm"] < plain["n_mvm"]
+    with pytest.raises(pkg.ChebFDError):
+        pkg.chebfd_solve(H, -delta, delta, NS, Np, a=-1.0, b=1.0, locking=True,
+                         extraction="harmonic")

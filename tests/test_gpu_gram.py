@@ -118,3 +118,61 @@ def test_gram_large_methods_agree(cplx):
     Gb = pkg.chebfd_gram(Q, method="fp64").cpu().numpy()
     assert np.abs(G - Gb).max() <= 2e-15
     assert np.abs(G - Q0.conj().T @ Q0).max() <= 2e-15 + 96 * 2.0 ** -53
+
+
+def exact_product(Y, M):
+    """Y @ M with every entry the correctly rounded sum of exact products."""
+    cplx = np.iscomplexobj(Y)
+    out = np.zeros((Y.shape[0], M.shape[1]), np.complex128 if cplx else np.float64)
+    Yr, Yi = np.real(Y), np.imag(Y) if cplx else np.zeros_like(Y)
+    Mr, Mi = np.real(M), np.imag(M) if cplx else np.zeros_like(M)
+
+    def dot(x, y):
+        p, e = _two_prod(x, y)
+        return np.concatenate([p, e])
+
+    for p_ in range(Y.shape[0]):
+        for i in range(M.shape[1]):
+            re = math.fsum(np.concatenate([dot(Yr[p_], Mr[:, i]), -dot(Yi[p_], Mi[:, i])]))
+            if cplx:
+                im = math.fsum(np.concatenate([dot(Yr[p_], Mi[:, i]), dot(Yi[p_], Mr[:, i])]))
+                out[p_, i] = re + 1j * im
+            else:
+                out[p_, i] = re
+    return out
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+@pytest.mark.parametrize("n,k,r", [(1, 1, 1), (127, 5, 7), (130, 48, 48), (64, 300, 9),
+                                   (257, 33, 70)])
+def test_block_update_small_against_exact_definition(cplx, n, k, r):
+    """T = Y M (the block update of steps 6-7) on ragged shapes: partial
+    128-row and 64-column tiles, k = 300 complex (K = 600 real: two 512-row
+    exact chunks), every entry within 2^-52 of |Y| |M| of the exactly rounded
+    product (tensor), cuBLAS and the double-float kernel within their bounds."""
+    Y0 = workloads.random_block(n + k, n, k, cplx)
+    M0 = workloads.random_block(n + k + r, k, r, cplx)
+    ref = exact_product(Y0, M0)
+    sc = np.abs(Y0) @ np.abs(M0)
+    Y, M = torch.from_numpy(Y0).to(DEV), torch.from_numpy(M0).to(DEV)
+    for method, tol in (("tensor", 2.0 ** -52), ("double_float", 2.0 ** -44),
+                        ("fp64", 2.0 ** -52 * k)):
+        T = pkg.chebfd_block_update(Y, M, method=method).cpu().numpy()
+        err = (np.abs(T - ref) / sc).max()
+        assert err <= tol, (method, err, tol)
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+def test_block_update_large_methods_agree(cplx):
+    """524288 x 192 times 192 x 192 (the benchmark's n_s), with rows of very
+    different scales (2^-200 .. 2^200): tensor and cuBLAS agree within 1e-14
+    of |Y| |M| row by row."""
+    n, k = 524288, 192
+    Y0 = workloads.random_block(41, n, k, cplx)
+    Y0 *= np.ldexp(1.0, (np.arange(n) % 401) - 200)[:, None]
+    M0 = workloads.random_block(42, k, k, cplx)
+    Y, M = torch.from_numpy(Y0).to(DEV), torch.from_numpy(M0).to(DEV)
+    Tt = pkg.chebfd_block_update(Y, M, method="tensor").cpu().numpy()
+    Tf = pkg.chebfd_block_update(Y, M, method="fp64").cpu().numpy()
+    sc = np.abs(Y0) @ np.abs(M0)
+    assert (np.abs(Tt - Tf) / sc).max() <= 1e-14

@@ -675,3 +675,50 @@ def test_chebfd_weak_filter_is_not_taken_for_an_empty_window():
     r = solve.chebfd(H, -1.001, 1.001, -0.02, 0.02, 32, 20, 1e-10, complex_values=False,
                      max_iter=12)
     assert not r["converged"] and r["iterations"] == 12
+
+
+def test_adaptive_degree_follows_the_linear_dos_rule():
+    """Adaptive N_p (Sec. 6 with the rule of Sec. 2.4): linear-DOS diagonal
+    matrix, D = 4000, window +-0.158 (N_T = D delta^2 = 100), N_S = 200,
+    started at N_p = 300.  The moments of the first filter give delta' close
+    to the linear-DOS value (sqrt(N_S / N_T) - 1) delta (the construction of
+    Tab. num) and N_p = N_0 / delta' with N_0 = 6.23 (Tab. lanczoskernel,
+    centre); all 100 eigenvalues are found, with fewer products than the run
+    that keeps N_p = 300."""
+    D, NS = 4000, 200
+    delta = np.sqrt(100.0 / D)
+    lam = lattice.linear_dos_eigs(D)
+    H = sp.diags(lam).tocsr()
+    r = solve.chebfd(H, -1.0, 1.0, -delta, delta, NS, 300, 1e-10, complex_values=False,
+                     adaptive=True)
+    NT, dprime, Np = r["adapted"]
+    want_dp = (np.sqrt(NS / 100.0) - 1.0) * delta
+    assert abs(NT - 100) <= 10
+    assert abs(dprime - want_dp) <= 0.1 * want_dp
+    assert abs(Np - 6.23 / want_dp) <= 0.1 * 6.23 / want_dp and r["Np"] == Np
+    exact = np.sort(lam[np.abs(lam) <= delta])
+    assert r["converged"] and len(r["theta"]) == len(exact) == 100
+    assert np.abs(np.sort(r["theta"]) - exact).max() < 1e-10
+    fixed = solve.chebfd(H, -1.0, 1.0, -delta, delta, NS, 300, 1e-10, complex_values=False)
+    assert fixed["converged"] and r["n_mvm"] < fixed["n_mvm"]
+
+
+def test_chebfd_locking_on_linear_dos():
+    """Hard locking (Sec. 6) on the linear-DOS diagonal (D = 4000, window
+    +-0.158 with N_T = 100, N_S = 200, N_p = 95): the eigenvalues near the
+    window centre converge first and are locked, four at a time; the search
+    block shrinks, the same 100 eigenvalues are found with orthonormal
+    vectors, and fewer products are needed than without locking."""
+    D, NS, Np = 4000, 200, 95
+    delta = np.sqrt(100.0 / D)
+    lam = lattice.linear_dos_eigs(D)
+    H = sp.diags(lam).tocsr()
+    plain = solve.chebfd(H, -1.0, 1.0, -delta, delta, NS, Np, 1e-10, complex_values=False)
+    r = solve.chebfd(H, -1.0, 1.0, -delta, delta, NS, Np, 1e-10, complex_values=False,
+                     locking=True)
+    exact = np.sort(lam[np.abs(lam) <= delta])
+    assert r["converged"] and len(r["theta"]) == len(exact) == 100
+    assert np.abs(np.sort(r["theta"]) - exact).max() <= 1e-10
+    assert np.abs(r["V"].T @ r["V"] - np.eye(100)).max() <= 1e-10
+    assert r["locked"] >= 4 and r["locked"] % 4 == 0
+    assert r["n_mvm"] < plain["n_mvm"]

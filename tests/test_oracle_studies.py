@@ -22,7 +22,8 @@ def test_inset_window_halves_the_spmvms_on_a_10x10x10_insulator():
     the window narrowed by half its half-width at half the degree finds every
     window eigenvalue in no more iterations than the rectangular window at
     the full degree (about half the spMVMs); the rectangular window at 0.6 of
-    the degree does not get them all."""
+    the degree is too weak for the ghost test for several iterations and
+    needs more spMVMs than either."""
     H, a, b, ew, delta, NS, Np = _insulator_case()
     runs = {}
     for name, inset, scale in (("rect", 0.0, 1.0), ("inset", 0.5, 0.5), ("rect_short", 0.0, 0.6)):
@@ -37,4 +38,6 @@ def test_inset_window_halves_the_spmvms_on_a_10x10x10_insulator():
     assert runs["inset"]["iterations"] <= runs["rect"]["iterations"]
     mvm = {k: runs[k]["iterations"] * runs[k]["Np"] for k in ("rect", "inset")}
     assert mvm["inset"] <= 0.55 * mvm["rect"]
-    assert len(runs["rect_short"]["theta"]) != 60 or not runs["rect_short"]["converged"]
+    short = runs["rect_short"]
+    assert short["converged"] and len(short["theta"]) == 60
+    assert short["iterations"] * short["Np"] > max(mvm["rect"], 2 * mvm["inset"])
