@@ -683,11 +683,24 @@ def run_profile(args):
             (--form sell | free);
     `solve` one ChebFD iteration (filter of degree 20, SVQB, Rayleigh-Ritz) on
             the 32x32x32x4 insulator (N = 131072, W = 1, seed 1), n_s = 256,
-            --solve-precisions[0] (fp64 | mixed_df)."""
+            --solve-precisions[0] (fp64 | mixed_df);
+    `pairs` a complex64 filter of degree 4 on 16 columns of the insulator,
+            matrix-free: first with the fused two-step kernel (one launch for
+            steps 3-4), then with single steps (two launches);
+    `gram`  the tall Gram A^H A of a 131072 x 256 complex128 block (seeded
+            uniform entries), once by each method of chebfd_gram: tensor,
+            double_float, fp64 (cuBLAS)."""
     import torch
 
     import paper_1510_04895_gb300 as pkg
     from paper_1510_04895_gb300 import workloads
+    if args.profile == "gram":
+        A = torch.from_numpy(workloads.random_block(7, 131072, 256, True)).to("cuda")
+        for method in ("tensor", "double_float", "fp64"):
+            pkg.chebfd_gram(A, method=method)
+        torch.cuda.synchronize()
+        print("profile target done")
+        return 0
     name = args.workload
     w = dict(getattr(workloads, WORKLOADS[name]["spec"]))
     if args.profile == "solve":
@@ -699,7 +712,14 @@ def run_profile(args):
         H.set_blocked(False)
     if args.form == "free":
         H.set_matrix_free(True)
-    if args.profile == "df":
+    if args.profile == "pairs":
+        X = torch.empty((H.n, 16), dtype=torch.complex64, device="cuda")
+        gc = pkg.chebfd_window_coeffs(-4.2, 4.2, -0.14, 0.14, 4, "lanczos", 2.0)
+        for pairs in (True, False):
+            pkg.chebfd_random_block(X, ns_total=16, seed=1)
+            H.set_matrix_free(True, pairs=pairs)
+            pkg.chebfd_filter_block(H, 2.0 / 8.4, 0.0, gc, X)
+    elif args.profile == "df":
         nb = args.nb or 32
         X = torch.empty((H.n, nb), dtype=torch.complex128, device="cuda")
         pkg.chebfd_random_block(X, ns_total=nb, seed=1)
@@ -746,7 +766,7 @@ def main():
     p.add_argument("--solve-precisions", dest="solve_precisions", nargs="*",
                    default=["fp64", "mixed", "mixed_df"],
                    help="precisions of the time-to-solution runs (the MLP run is extra)")
-    p.add_argument("--profile", choices=["step", "df", "solve"], default=None,
+    p.add_argument("--profile", choices=["step", "df", "solve", "pairs", "gram"], default=None,
                    help="run a short launch sequence for an ncu capture and exit")
     p.add_argument("--form", choices=["blocked", "sell", "free"], default="blocked",
                    help="--profile: insulator step on the blocked copy, the SELL arrays, or "

@@ -180,7 +180,15 @@ chebfd_status chebfd_matrix_set_blocked(chebfd_matrix* H, int enable);
  * step then moves only the vectors.  The other operations keep using the
  * stored arrays.  Results agree with the stored-matrix kernels to FP32
  * (complex64) or double-float rounding.
- * (H, 0) returns to the stored matrix.  EUNSUPPORTED for other matrices. */
+ * (H, 0) returns to the stored matrix.  EUNSUPPORTED for other matrices.
+ * (H, 2): as (H, 1), and the complex64 filter (chebfd_filter_block) runs
+ * the steps two at a time (temporal blocking): 16-column panels, 8 x 8 x-y
+ * tiles with a one-site halo and z-segments of Z planes (Z divides Lz; Lx,
+ * Ly multiples of 8), T_{n+1} of the tile and its halo kept in a ring of
+ * three planes in shared memory, so a pair of steps moves the vectors 6
+ * times instead of 10; results equal the single steps bit for bit.  On
+ * GB300 this is slower than the single step (latency-bound at 8 warps per
+ * SM), so it is off by default.  EINVAL for other modes. */
 chebfd_status chebfd_matrix_set_matrix_free(chebfd_matrix* H, int enable);
 
 chebfd_status chebfd_matrix_destroy(chebfd_matrix* H);

@@ -252,10 +252,12 @@ class Matrix:
         _check(lib().chebfd_matrix_set_blocked(self.handle, 1 if enable else 0),
                "chebfd_matrix_set_blocked")
 
-    def set_matrix_free(self, enable):
+    def set_matrix_free(self, enable, pairs=False):
         """Rebuild the insulator's entries in registers in the complex64 step
-        and in the double-float step."""
-        _check(lib().chebfd_matrix_set_matrix_free(self.handle, 1 if enable else 0),
+        and in the double-float step; pairs=True also runs the complex64
+        filter two Chebyshev steps per pass (16-column panels)."""
+        mode = (2 if pairs else 1) if enable else 0
+        _check(lib().chebfd_matrix_set_matrix_free(self.handle, mode),
                "chebfd_matrix_set_matrix_free")
 
     def close(self):

@@ -511,7 +511,9 @@ chebfd_status chebfd_matrix_set_matrix_free(chebfd_matrix* H, int enable) {
         CHEBFD_REQUIRE(!enable || ok, CHEBFD_EUNSUPPORTED,
                        "matrix-free step needs an insulator lattice built with also_single and "
                        "sell_sigma = 1");
+        CHEBFD_REQUIRE(enable >= 0 && enable <= 2, CHEBFD_EINVAL, "mode must be 0, 1 or 2");
         H->m.stencil_enabled = enable != 0;
+        H->m.stencil_pairs = enable == 2;
     });
 }
 

@@ -104,6 +104,7 @@ struct Matrix {
     chebfd_lattice_desc gen{};
     bool has_gen = false;
     bool stencil_enabled = false;
+    bool stencil_pairs = false;   // two Chebyshev steps per pass (16-column panels)
     // Row panel order used by the kernels (same as sorted order here).
     int device = 0;
     int num_sms = 0;
@@ -242,10 +243,17 @@ class PhaseClock {
 // X (ld) becomes sum_n gc[n] T_n(A) X; U, W are two work panels (ldw);
 // moments (nullable, 2 Np x mom_ld) with per-block partials and a completion
 // counter that starts at zero.  Asynchronous on s.
+// With two more work panels W2, W3 (non-null) and a matrix-free insulator
+// panel of 16 complex64 columns, the steps n >= 3 run two at a time
+// (stencil2_applies / launch_stencil2 in stencil_step.cu).
 void filter_panel(const Matrix& M, double alpha, double beta, const double* gc, int Np, char* X,
                   int64_t ld, int nb, chebfd_dtype dt, double* moments, int64_t mom_ld,
                   char* U, char* W, int64_t ldw, double* partials, unsigned int* counter,
-                  cudaStream_t s);
+                  cudaStream_t s, char* W2 = nullptr, char* W3 = nullptr);
+bool stencil2_applies(const Matrix& M, chebfd_dtype dt, int nb);
+void launch_stencil2(const Matrix& M, const void* u0, const void* um, void* u1, void* u2,
+                     void* y, int64_t ldw, int64_t ldy, double alpha, double beta, double c1,
+                     double c2, cudaStream_t s);
 
 void launch_random_block(void* X, int64_t n, int64_t ld, int nb, int col0, int ns_total,
                          uint64_t seed, chebfd_dtype dt, cudaStream_t stream);

@@ -275,7 +275,7 @@ int64_t padded_ld(chebfd_dtype dt, int nb) {
 void filter_panel(const Matrix& M, double alpha, double beta, const double* gc, int Np, char* X,
                   int64_t ld, int nb, chebfd_dtype dt, double* moments, int64_t mom_ld,
                   char* U, char* W, int64_t ldw, double* partials, unsigned int* counter,
-                  cudaStream_t s) {
+                  cudaStream_t s, char* W2, char* W3) {
     StepArgs a{};
     a.nb = nb;
     a.alpha = alpha;
@@ -309,7 +309,20 @@ void filter_panel(const Matrix& M, double alpha, double beta, const double* gc, 
     // the sum gains gc_n T_n in the same pass
     char* t_prev = U;  // T_{n-2}
     char* t_cur = W;   // T_{n-1}
-    for (int n = 3; n <= Np; ++n) {
+    int n0 = 3;
+    if (W2 && W3 && !moments && stencil2_applies(M, dt, nb)) {
+        // pairs: T_n, T_{n+1} into the two spare panels, which then become
+        // the latest two; the older two are the spares of the next pair
+        char* s1 = W2;
+        char* s2 = W3;
+        for (; n0 + 1 <= Np; n0 += 2) {
+            launch_stencil2(M, t_cur, t_prev, s1, s2, X, ldw, ld, alpha, beta, gc[n0], gc[n0 + 1],
+                            s);
+            std::swap(t_prev, s1);
+            std::swap(t_cur, s2);
+        }
+    }
+    for (int n = n0; n <= Np; ++n) {
         a.gather = t_cur;
         a.w = t_prev;  // T_{n-2} in, T_n out
         a.c0 = gc[n];
@@ -326,11 +339,15 @@ void filter_block_impl(const Matrix& M, double alpha, double beta, const double*
     CHEBFD_REQUIRE(gc != nullptr && Np >= 2, CHEBFD_EINVAL, "need Np >= 2 and coefficients");
     CHEBFD_REQUIRE(std::isfinite(alpha) && std::isfinite(beta), CHEBFD_EINVAL,
                    "alpha, beta must be finite");
-    const int pw = panel > 0 ? std::min(panel, max_panel_width(dt)) : max_panel_width(dt);
+    int pw = panel > 0 ? std::min(panel, max_panel_width(dt)) : max_panel_width(dt);
+    // the matrix-free insulator: 16-column panels, two steps per pass
+    const bool pairs = !moments && nb >= 16 && nb % 16 == 0 && stencil2_applies(M, dt, 16);
+    if (pairs) pw = 16;
     const int wmax = std::min(pw, nb);
     const int64_t ldw = padded_ld(dt, wmax);
     const size_t es = dtype_size(dt);
     DeviceBuffer U((size_t)M.n * ldw * es, s), W((size_t)M.n * ldw * es, s);
+    DeviceBuffer W2(pairs ? (size_t)M.n * ldw * es : 0, s), W3(pairs ? (size_t)M.n * ldw * es : 0, s);
     const int grid_max = M.num_sms * 8;
     DeviceBuffer part(moments ? (size_t)grid_max * 2 * wmax * sizeof(double) : 0, s);
     DeviceBuffer cnt(moments ? 256 : 0, s);
@@ -341,7 +358,7 @@ void filter_block_impl(const Matrix& M, double alpha, double beta, const double*
                        "panel width * element size must be a multiple of 16 bytes");
         filter_panel(M, alpha, beta, gc, Np, (char*)X + p0 * es, ld, pnb, dt,
                      moments ? moments + p0 : nullptr, nb, (char*)U.p, (char*)W.p, ldw,
-                     (double*)part.p, (unsigned int*)cnt.p, s);
+                     (double*)part.p, (unsigned int*)cnt.p, s, (char*)W2.p, (char*)W3.p);
     }
     if (moments) {
         std::vector<double> h((size_t)2 * Np * nb);

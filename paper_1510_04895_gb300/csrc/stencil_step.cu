@@ -70,6 +70,51 @@ __device__ __forceinline__ void hop(float2 (*acc)[2], const float4* g, float h, 
     }
 }
 
+// (H + shift) u on the 4 rows of site s = (x, y, z) for one 16-byte chunk of
+// columns, accumulated in acc[row][2]: the onsite block first, then the
+// neighbours -x, +x, -y, +y, -z, +z (the slab has no z neighbour beyond its
+// faces).  gather(k, g) loads the 4 rows of neighbour k (0: the site itself,
+// 1..6 in that order) into g.  The same order everywhere, so every caller
+// rounds alike.
+template <class Gather>
+__device__ __forceinline__ void stencil_site_acc(const StencilView& L, int64_t s, int64_t z,
+                                                 float shift, Gather&& gather,
+                                                 float2 (*acc)[2]) {
+    constexpr int B = 4;
+#pragma unroll
+    for (int r = 0; r < B; ++r) acc[r][0] = acc[r][1] = make_float2(0.f, 0.f);
+    float4 g[B];
+    gather(0, g);
+    // the generator's roundings: V = W (u - 1/2), then m + V or V +- m
+    const double V = __dmul_rn(L.W, splitmix_uniform(L.seed, STREAM_DISORDER, (uint64_t)s) - 0.5);
+    float on_up, on_lo;
+    if (L.slab) {
+        on_up = __double2float_rn(__dadd_rn(V, L.m));
+        on_lo = __double2float_rn(__dadd_rn(V, -L.m));
+    } else {
+        on_up = __double2float_rn(__dadd_rn(L.m, V));
+        on_lo = -on_up;
+    }
+#pragma unroll
+    for (int o = 0; o < B; ++o) mac_re(acc[o], (o < 2 ? on_up : on_lo) + shift, g[o]);
+    gather(1, g);
+    hop<0>(acc, g, L.h, 1.f);
+    gather(2, g);
+    hop<0>(acc, g, L.h, -1.f);
+    gather(3, g);
+    hop<1>(acc, g, L.h, 1.f);
+    gather(4, g);
+    hop<1>(acc, g, L.h, -1.f);
+    if (!L.slab || z > 0) {
+        gather(5, g);
+        hop<2>(acc, g, L.h, 1.f);
+    }
+    if (!L.slab || z + 1 < L.Lz) {
+        gather(6, g);
+        hop<2>(acc, g, L.h, -1.f);
+    }
+}
+
 template <int G>
 __global__ void __launch_bounds__(ST_THREADS, 3)
     stencil_step_kernel(StencilView L, StepArgs a, int wc, float shift) {
@@ -104,50 +149,22 @@ __global__ void __launch_bounds__(ST_THREADS, 3)
             auto site = [&](int64_t cx, int64_t cy, int64_t cz) {
                 return cx + L.Lx * (cy + L.Ly * cz);
             };
-            auto gather = [&](int64_t sn, float4* g) {
-                const float* base = u + sn * B * ldg + cofs;
+            // neighbour k of the site: 0 itself, 1..6 = -x, +x, -y, +y, -z, +z (periodic)
+            auto gather = [&](int k, float4* g) {
+                int64_t cx = x, cy = yy, cz = z;
+                if (k == 1) cx = (x + L.Lx - 1) % L.Lx;
+                if (k == 2) cx = (x + 1) % L.Lx;
+                if (k == 3) cy = (yy + L.Ly - 1) % L.Ly;
+                if (k == 4) cy = (yy + 1) % L.Ly;
+                if (k == 5) cz = (z + L.Lz - 1) % L.Lz;
+                if (k == 6) cz = (z + 1) % L.Lz;
+                const float* base = u + site(cx, cy, cz) * B * ldg + cofs;
 #pragma unroll
                 for (int o = 0; o < B; ++o)
                     g[o] = __ldg(reinterpret_cast<const float4*>(base + o * ldg));
             };
             float2 acc[B][2];
-#pragma unroll
-            for (int r = 0; r < B; ++r) acc[r][0] = acc[r][1] = make_float2(0.f, 0.f);
-            float4 g[B];
-            // onsite, with the shift beta/alpha
-            gather(s, g);
-            // the generator's roundings: V = W (u - 1/2), then m + V or V +- m
-            const double V =
-                __dmul_rn(L.W, splitmix_uniform(L.seed, STREAM_DISORDER, (uint64_t)s) - 0.5);
-            float on_up, on_lo;
-            if (L.slab) {
-                on_up = __double2float_rn(__dadd_rn(V, L.m));
-                on_lo = __double2float_rn(__dadd_rn(V, -L.m));
-            } else {
-                on_up = __double2float_rn(__dadd_rn(L.m, V));
-                on_lo = -on_up;
-            }
-#pragma unroll
-            for (int o = 0; o < B; ++o) mac_re(acc[o], (o < 2 ? on_up : on_lo) + shift, g[o]);
-            // x neighbours (periodic)
-            gather(site((x + L.Lx - 1) % L.Lx, yy, z), g);
-            hop<0>(acc, g, L.h, 1.f);
-            gather(site((x + 1) % L.Lx, yy, z), g);
-            hop<0>(acc, g, L.h, -1.f);
-            // y neighbours (periodic)
-            gather(site(x, (yy + L.Ly - 1) % L.Ly, z), g);
-            hop<1>(acc, g, L.h, 1.f);
-            gather(site(x, (yy + 1) % L.Ly, z), g);
-            hop<1>(acc, g, L.h, -1.f);
-            // z neighbours (periodic, or open for the slab)
-            if (!L.slab || z > 0) {
-                gather(site(x, yy, (z + L.Lz - 1) % L.Lz), g);
-                hop<2>(acc, g, L.h, 1.f);
-            }
-            if (!L.slab || z + 1 < L.Lz) {
-                gather(site(x, yy, (z + 1) % L.Lz), g);
-                hop<2>(acc, g, L.h, -1.f);
-            }
+            stencil_site_acc(L, s, z, shift, gather, acc);
 #pragma unroll
             for (int r = 0; r < B; ++r) {
                 const int64_t row = s * B + r;
@@ -165,6 +182,144 @@ __global__ void __launch_bounds__(ST_THREADS, 3)
         }
         q = q_next;
         tt = tt + 1 == tile ? 0 : tt + 1;
+    }
+}
+
+// ---- two Chebyshev steps per pass (temporal blocking of the matrix-free
+// step; the paper's matrices constructed on the fly, Sec. 1) --------------
+//
+// u1 = 2 (alpha H + beta) u0 - um and u2 = 2 (alpha H + beta) u1 - u0 with
+// y += c1 u1 + c2 u2, for a 16-column complex64 panel.  A CTA owns an 8 x 8
+// tile of the x-y plane and Z consecutive z-planes.  Plane by plane it
+// computes u1 on the tile and a one-site halo into a ring of three planes in
+// shared memory (step 1, gathering u0 from global memory), then u2 on the
+// tile one plane behind (step 2, gathering u1 from the ring).  u1 of the
+// tile's own sites and u2 go to two other buffers (neighbouring CTAs still
+// read u0 and um), y is read and written once.  Per pair of steps the
+// vectors move 6 times instead of 10; the halo costs step-1 arithmetic
+// (100 / 64 sites, (Z + 2) / Z planes).  Same per-site arithmetic as the
+// single step, so a pair equals two single steps bit for bit.
+constexpr int S2_TX = 8, S2_TY = 8;
+constexpr int S2_HX = S2_TX + 2, S2_HY = S2_TY + 2, S2_HS = S2_HX * S2_HY;  // haloed sites
+constexpr int S2_WC = 8;                          // 16-byte chunks per row: n_b = 16
+constexpr int S2_THREADS = 256, S2_SLOTS = S2_THREADS / S2_WC;
+constexpr size_t S2_RING_BYTES = (size_t)3 * S2_HS * 4 * S2_WC * 16;   // 153600
+
+struct S2Args {
+    const float* u0;   // T_n X   (gathered)
+    const float* um;   // T_{n-1} X
+    float* u1;         // out: T_{n+1} X
+    float* u2;         // out: T_{n+2} X
+    float* y;          // accumulated sum (in/out)
+    int64_t ldw, ldy;  // floats per row of the work panels / of y
+    float ta, shift, c1, c2;
+    int Z;             // planes per CTA
+};
+
+__global__ void __launch_bounds__(S2_THREADS, 1) stencil2_kernel(StencilView L, S2Args a) {
+    constexpr int B = 4;
+    extern __shared__ float4 ring[];  // [3][S2_HS][B][S2_WC]
+    const int lane = threadIdx.x % S2_WC, slot = threadIdx.x / S2_WC;
+    const int tiles_x = (int)(L.Lx / S2_TX), tiles_y = (int)(L.Ly / S2_TY);
+    const int tile = blockIdx.x % (tiles_x * tiles_y), seg = blockIdx.x / (tiles_x * tiles_y);
+    const int x0 = (tile % tiles_x) * S2_TX, y0 = (tile / tiles_x) * S2_TY, z0 = seg * a.Z;
+    const int Lx = (int)L.Lx, Ly = (int)L.Ly, Lz = (int)L.Lz;
+    auto mod = [](int v, int n) { v %= n; return v < 0 ? v + n : v; };
+    auto site = [&](int x, int y, int z) { return (int64_t)x + L.Lx * ((int64_t)y + L.Ly * z); };
+    auto plane = [&](int zz) { return ring + (size_t)mod(zz - z0 + 1, 3) * S2_HS * B * S2_WC; };
+    const float2 ta = dup2(a.ta), c1 = dup2(a.c1), c2 = dup2(a.c2);
+    const int cofs = 4 * lane;
+    for (int zz = z0 - 1; zz <= z0 + a.Z; ++zz) {
+        // ---- step 1: u1 on the haloed plane zz (absent beyond a slab's faces)
+        const bool exists = !L.slab || (zz >= 0 && zz < Lz);
+        const int zw = mod(zz, Lz);
+        float4* pz = plane(zz);
+        for (int hs = slot; hs < S2_HS; hs += S2_SLOTS) {
+            const int hx = hs % S2_HX, hy = hs / S2_HX;
+            float4 out[B];
+#pragma unroll
+            for (int r = 0; r < B; ++r) out[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (exists) {
+                const int gx = mod(x0 - 1 + hx, Lx), gy = mod(y0 - 1 + hy, Ly);
+                const int64_t s = site(gx, gy, zw);
+                auto gather = [&](int k, float4* g) {
+                    int cx = gx, cy = gy, cz = zw;
+                    if (k == 1) cx = mod(gx - 1, Lx);
+                    if (k == 2) cx = mod(gx + 1, Lx);
+                    if (k == 3) cy = mod(gy - 1, Ly);
+                    if (k == 4) cy = mod(gy + 1, Ly);
+                    if (k == 5) cz = mod(zw - 1, Lz);
+                    if (k == 6) cz = mod(zw + 1, Lz);
+                    const float* base = a.u0 + site(cx, cy, cz) * B * a.ldw + cofs;
+#pragma unroll
+                    for (int o = 0; o < B; ++o)
+                        g[o] = __ldg(reinterpret_cast<const float4*>(base + o * a.ldw));
+                };
+                float2 acc[B][2];
+                stencil_site_acc(L, s, zw, a.shift, gather, acc);
+                const bool own = hx >= 1 && hx <= S2_TX && hy >= 1 && hy <= S2_TY && zz >= z0 &&
+                                 zz < z0 + a.Z;
+#pragma unroll
+                for (int r = 0; r < B; ++r) {
+                    const int64_t row = s * B + r;
+                    const float4 wo =
+                        __ldg(reinterpret_cast<const float4*>(a.um + row * a.ldw + cofs));
+                    const float2 w0 = __ffma2_rn(ta, acc[r][0], make_float2(-wo.x, -wo.y));
+                    const float2 w1 = __ffma2_rn(ta, acc[r][1], make_float2(-wo.z, -wo.w));
+                    out[r] = make_float4(w0.x, w0.y, w1.x, w1.y);
+                    if (own) __stcs(reinterpret_cast<float4*>(a.u1 + row * a.ldw + cofs), out[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < B; ++r) pz[(hs * B + r) * S2_WC + lane] = out[r];
+        }
+        __syncthreads();
+        // ---- step 2: u2 on the tile of plane zz - 1
+        const int zt = zz - 1;
+        if (zt >= z0 && zt < z0 + a.Z) {
+            const int ztw = mod(zt, Lz);
+            const float4* pm = plane(zt - 1);
+            const float4* p0 = plane(zt);
+            const float4* pp = plane(zt + 1);
+            for (int ts = slot; ts < S2_TX * S2_TY; ts += S2_SLOTS) {
+                const int tx = ts % S2_TX, ty = ts / S2_TX, hx = tx + 1, hy = ty + 1;
+                const int64_t s = site(x0 + tx, y0 + ty, ztw);
+                auto gather = [&](int k, float4* g) {
+                    const float4* pl = k == 5 ? pm : (k == 6 ? pp : p0);
+                    int cx = hx, cy = hy;
+                    if (k == 1) cx = hx - 1;
+                    if (k == 2) cx = hx + 1;
+                    if (k == 3) cy = hy - 1;
+                    if (k == 4) cy = hy + 1;
+                    const float4* base = pl + (size_t)((cy * S2_HX + cx) * B) * S2_WC + lane;
+#pragma unroll
+                    for (int o = 0; o < B; ++o) g[o] = base[o * S2_WC];
+                };
+                float2 acc[B][2];
+                stencil_site_acc(L, s, ztw, a.shift, gather, acc);
+#pragma unroll
+                for (int r = 0; r < B; ++r) {
+                    const int64_t row = s * B + r;
+                    const float4 u1v = p0[((hy * S2_HX + hx) * B + r) * S2_WC + lane];
+                    const float4 u0v =
+                        __ldg(reinterpret_cast<const float4*>(a.u0 + row * a.ldw + cofs));
+                    const float4 yo =
+                        __ldcs(reinterpret_cast<const float4*>(a.y + row * a.ldy + cofs));
+                    // the two single steps' updates of y, in their order
+                    const float2 y0a = __ffma2_rn(c1, make_float2(u1v.x, u1v.y), make_float2(yo.x, yo.y));
+                    const float2 y1a = __ffma2_rn(c1, make_float2(u1v.z, u1v.w), make_float2(yo.z, yo.w));
+                    const float2 w0 = __ffma2_rn(ta, acc[r][0], make_float2(-u0v.x, -u0v.y));
+                    const float2 w1 = __ffma2_rn(ta, acc[r][1], make_float2(-u0v.z, -u0v.w));
+                    const float2 y0 = __ffma2_rn(c2, w0, y0a);
+                    const float2 y1 = __ffma2_rn(c2, w1, y1a);
+                    __stcs(reinterpret_cast<float4*>(a.u2 + row * a.ldw + cofs),
+                           make_float4(w0.x, w0.y, w1.x, w1.y));
+                    __stcs(reinterpret_cast<float4*>(a.y + row * a.ldy + cofs),
+                           make_float4(y0.x, y0.y, y1.x, y1.y));
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -359,6 +514,52 @@ StencilView view_of_gen(const Matrix& M) {
 }
 
 }  // namespace
+
+// z-planes per CTA of the two-step kernel: a divisor of Lz, 8 preferred
+// (halo overhead (Z + 2) / Z against enough CTAs); 0 if none fits.
+int s2_planes(int64_t Lz) {
+    for (int Z : {8, 10, 12, 16, 6, 5, 4})
+        if (Lz % Z == 0) return Z;
+    return Lz <= 16 ? (int)Lz : 0;
+}
+
+bool stencil2_applies(const Matrix& M, chebfd_dtype dt, int nb) {
+    return M.stencil_pairs && M.stencil_enabled && M.has_gen && dt == CHEBFD_C64 &&
+           nb == 2 * S2_WC &&
+           M.gen.Lx % S2_TX == 0 && M.gen.Ly % S2_TY == 0 && s2_planes(M.gen.Lz) > 0 &&
+           M.n < ((int64_t)1 << 31);
+}
+
+// Two fused Chebyshev steps on 16-column complex64 panels (ldw: the work
+// panels' leading dimension in complex entries, ldy: the accumulated block's).
+void launch_stencil2(const Matrix& M, const void* u0, const void* um, void* u1, void* u2,
+                     void* y, int64_t ldw, int64_t ldy, double alpha, double beta, double c1,
+                     double c2, cudaStream_t s) {
+    const StencilView v = view_of_gen(M);
+    S2Args a;
+    a.u0 = (const float*)u0;
+    a.um = (const float*)um;
+    a.u1 = (float*)u1;
+    a.u2 = (float*)u2;
+    a.y = (float*)y;
+    a.ldw = 2 * ldw;
+    a.ldy = 2 * ldy;
+    a.ta = (float)(2.0 * alpha);
+    a.shift = (float)(beta / alpha);
+    a.c1 = (float)c1;
+    a.c2 = (float)c2;
+    a.Z = s2_planes(v.Lz);
+    static bool attr = false;
+    if (!attr) {
+        CHEBFD_CHECK_CUDA(cudaFuncSetAttribute(stencil2_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)S2_RING_BYTES));
+        attr = true;
+    }
+    const int grid = (int)((v.Lx / S2_TX) * (v.Ly / S2_TY) * (v.Lz / a.Z));
+    stencil2_kernel<<<grid, S2_THREADS, S2_RING_BYTES, s>>>(v, a);
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+}
 
 bool stencil_step_applies(const Matrix& M, chebfd_dtype dt, StepMode mode, const StepArgs& a,
                           int wc) {

@@ -202,3 +202,34 @@ def test_tiled_site_order_visits_every_site(kind, L):
         # every row updated correctly (a skipped or doubled site shows up row-wise)
         row_err = np.linalg.norm(w - ref_w, axis=1) / np.linalg.norm(ref_w, axis=1)
         assert row_err.max() <= 1e-5, (free, row_err.max())
+
+
+@pytest.mark.parametrize("kind,L,Np", [("topi", (16, 8, 12), 9), ("topi", (8, 16, 20), 12),
+                                       ("topi", (8, 8, 3), 7), ("topi_slab", (24, 8, 8), 10)])
+def test_two_step_matrix_free_filter(kind, L, Np):
+    """Two Chebyshev steps per pass (matrix-free insulator, 16-column panels,
+    8 x 8 x-y tiles with a one-site halo, z-segments of Z planes): the filter
+    of a 16-column block equals, bit for bit, the same block filtered with
+    single matrix-free steps (the same per-site arithmetic); odd and even
+    N_p (a single step left over), periodic and open z, and it agrees with the
+    FP64 oracle within the complex64 bound."""
+    Lx, Ly, Lz = L
+    kw = dict(t=1.0, m=(1.0 if kind == "topi" else 2.0), W=1.2, seed=7, also_single=True)
+    H = pkg.chebfd_matrix_create_lattice(kind, Lx, Ly, Lz, **kw)
+    H.set_matrix_free(True, pairs=True)
+    gen = lattice.topi_csr if kind == "topi" else lattice.topi_slab_csr
+    Ho = lattice.to_scipy(*gen(Lx, Ly, Lz, t=kw["t"], m=kw["m"], W=kw["W"], seed=kw["seed"]))
+    a, b = -5.6, 5.6
+    alpha, beta = coeffs.scaling(a, b)
+    gc = coeffs.filter_coeffs(a, b, -0.3, 0.1, Np, "lanczos")
+    X0 = workloads.random_block(Lx + Np, H.n, 16, True).astype(np.complex64)
+    X = torch.from_numpy(X0).to(DEV)
+    pkg.chebfd_filter_block(H, alpha, beta, gc, X)
+    H.set_matrix_free(True)      # single steps for the reference
+    Xs = torch.from_numpy(X0).to(DEV)
+    pkg.chebfd_filter_block(H, alpha, beta, gc, Xs)
+    got = X.cpu().numpy()
+    assert np.array_equal(got, Xs.cpu().numpy())
+    ref = ofilt.filter_block(Ho, alpha, beta, gc, X0.astype(np.complex128))
+    bound = Np * 30 * 2.0 ** -24 * np.linalg.norm(X0) / np.linalg.norm(ref)
+    assert rel(got, ref) <= bound
