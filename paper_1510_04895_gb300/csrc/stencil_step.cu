@@ -14,6 +14,7 @@
 // -(t/2) Gamma1[o][o] and to its Gamma_{j+1} partner p with a purely real or
 // purely imaginary value.  Only the vectors move: 5 n_b S_v bytes per row.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 
 #include "async_copy.cuh"
@@ -372,8 +373,41 @@ __device__ __forceinline__ void hop_df(DFPair* acc, const float4* g, float h1, f
     }
 }
 
+// Unit-coefficient hopping sums of one neighbour (axis J, q = +1 below, -1
+// above) for the exact-hopping path: with every hopping value +-h or +-i h,
+// row o of H u gathers h S_o, where S_o sums the terms -+ g[o] of every
+// neighbour and the partner terms (x: q i g[o^3], y: +-g[o^3], z: +-i
+// g[o^2]).  The coefficients are +-1 and +-i, so each term is an error-free
+// add (df_add_scaled); an imaginary term enters with its components
+// swapped, i (a + i b) = (-b, a).
+template <int J>
+__device__ __forceinline__ void hop_sum_df(DFPair* S, const float4* g, float q, bool first) {
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        const float sd = o < 2 ? -1.f : 1.f;
+        const float sp = (o == 0 || o == 2) ? q : -q;
+        const DFPair go = df_pair(g[o]);
+        if (first) {
+            S[o].hi = __fmul2_rn(make_float2(sd, sd), go.hi);
+            S[o].lo = __fmul2_rn(make_float2(sd, sd), go.lo);
+        } else {
+            df_add_scaled(S[o], make_float2(sd, sd), go);
+        }
+        if (J == 0 || J == 2) {
+            const float4 c = g[J == 0 ? o ^ 3 : o ^ 2];
+            const float sg = J == 0 ? q : sp;
+            const DFPair ic = {make_float2(c.y, c.x), make_float2(c.w, c.z)};
+            df_add_scaled(S[o], make_float2(-sg, sg), ic);
+        } else {
+            df_add_scaled(S[o], make_float2(sp, sp), df_pair(g[o ^ 3]));
+        }
+    }
+}
+
 // a.ldg / a.ldw / a.ldy in 16-byte chunks (one double-float complex entry).
-template <int G, int MINB>
+// EXACT: the hopping t/2 is a power of two (no low word, every product by it
+// exact), so the hops are summed with unit coefficients and scaled once.
+template <int G, int MINB, bool EXACT>
 __global__ void __launch_bounds__(ST_THREADS, MINB)
     stencil_df_kernel(StencilView L, StepArgs a, int wc, double shift) {
     constexpr int B = 4, SLOTS = ST_THREADS / G;
@@ -414,10 +448,7 @@ __global__ void __launch_bounds__(ST_THREADS, MINB)
                 for (int o = 0; o < B; ++o) g[o] = __ldg(u + (sn * B + o) * ldg + lane);
             };
             DFPair acc[B];
-#pragma unroll
-            for (int r = 0; r < B; ++r) acc[r].hi = acc[r].lo = make_float2(0.f, 0.f);
             float4 g[B];
-            gather(s, g);
             const double V =
                 __dmul_rn(L.W, splitmix_uniform(L.seed, STREAM_DISORDER, (uint64_t)s) - 0.5);
             double up, lo;
@@ -431,24 +462,54 @@ __global__ void __launch_bounds__(ST_THREADS, MINB)
             float up1, up2, lo1, lo2;
             df_split(up + shift, up1, up2);
             df_split(lo + shift, lo1, lo2);
+            if constexpr (EXACT) {
+                DFPair S[B];
+                gather(site((x + L.Lx - 1) % L.Lx, yy, z), g);
+                hop_sum_df<0>(S, g, 1.f, true);
+                gather(site((x + 1) % L.Lx, yy, z), g);
+                hop_sum_df<0>(S, g, -1.f, false);
+                gather(site(x, (yy + L.Ly - 1) % L.Ly, z), g);
+                hop_sum_df<1>(S, g, 1.f, false);
+                gather(site(x, (yy + 1) % L.Ly, z), g);
+                hop_sum_df<1>(S, g, -1.f, false);
+                if (!L.slab || z > 0) {
+                    gather(site(x, yy, (z + L.Lz - 1) % L.Lz), g);
+                    hop_sum_df<2>(S, g, 1.f, false);
+                }
+                if (!L.slab || z + 1 < L.Lz) {
+                    gather(site(x, yy, (z + 1) % L.Lz), g);
+                    hop_sum_df<2>(S, g, -1.f, false);
+                }
+                gather(s, g);
 #pragma unroll
-            for (int o = 0; o < B; ++o)
-                df_mac(acc[o], o < 2 ? up1 : lo1, o < 2 ? up2 : lo2, df_pair(g[o]));
-            gather(site((x + L.Lx - 1) % L.Lx, yy, z), g);
-            hop_df<0>(acc, g, h1, h2, 1.f);
-            gather(site((x + 1) % L.Lx, yy, z), g);
-            hop_df<0>(acc, g, h1, h2, -1.f);
-            gather(site(x, (yy + L.Ly - 1) % L.Ly, z), g);
-            hop_df<1>(acc, g, h1, h2, 1.f);
-            gather(site(x, (yy + 1) % L.Ly, z), g);
-            hop_df<1>(acc, g, h1, h2, -1.f);
-            if (!L.slab || z > 0) {
-                gather(site(x, yy, (z + L.Lz - 1) % L.Lz), g);
-                hop_df<2>(acc, g, h1, h2, 1.f);
-            }
-            if (!L.slab || z + 1 < L.Lz) {
-                gather(site(x, yy, (z + 1) % L.Lz), g);
-                hop_df<2>(acc, g, h1, h2, -1.f);
+                for (int o = 0; o < B; ++o) {
+                    acc[o].hi = __fmul2_rn(make_float2(h1, h1), S[o].hi);
+                    acc[o].lo = __fmul2_rn(make_float2(h1, h1), S[o].lo);
+                    df_mac(acc[o], o < 2 ? up1 : lo1, o < 2 ? up2 : lo2, df_pair(g[o]));
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < B; ++r) acc[r].hi = acc[r].lo = make_float2(0.f, 0.f);
+                gather(s, g);
+#pragma unroll
+                for (int o = 0; o < B; ++o)
+                    df_mac(acc[o], o < 2 ? up1 : lo1, o < 2 ? up2 : lo2, df_pair(g[o]));
+                gather(site((x + L.Lx - 1) % L.Lx, yy, z), g);
+                hop_df<0>(acc, g, h1, h2, 1.f);
+                gather(site((x + 1) % L.Lx, yy, z), g);
+                hop_df<0>(acc, g, h1, h2, -1.f);
+                gather(site(x, (yy + L.Ly - 1) % L.Ly, z), g);
+                hop_df<1>(acc, g, h1, h2, 1.f);
+                gather(site(x, (yy + 1) % L.Ly, z), g);
+                hop_df<1>(acc, g, h1, h2, -1.f);
+                if (!L.slab || z > 0) {
+                    gather(site(x, yy, (z + L.Lz - 1) % L.Lz), g);
+                    hop_df<2>(acc, g, h1, h2, 1.f);
+                }
+                if (!L.slab || z + 1 < L.Lz) {
+                    gather(site(x, yy, (z + 1) % L.Lz), g);
+                    hop_df<2>(acc, g, h1, h2, -1.f);
+                }
             }
 #pragma unroll
             for (int r = 0; r < B; ++r) {
@@ -472,13 +533,19 @@ __global__ void __launch_bounds__(ST_THREADS, MINB)
     }
 }
 
-template <int G, int MINB>
+template <int G, int MINB, bool EXACT>
 void launch_df_gm(const StencilView& v, const StepArgs& a, int wc, double shift, int sms,
                   cudaStream_t s) {
-    auto kern = stencil_df_kernel<G, MINB>;
+    auto kern = stencil_df_kernel<G, MINB, EXACT>;
     const int grid =
         sms * std::min(8, cached_occupancy(reinterpret_cast<const void*>(kern), ST_THREADS, 0));
     kern<<<grid, ST_THREADS, 0, s>>>(v, a, wc, shift);
+}
+
+// t/2 a power of two: no low word and every product by it exact.
+bool exact_hopping(double hd) {
+    int e = 0;
+    return hd != 0.0 && std::fabs(std::frexp(hd, &e)) == 0.5 && e > -120 && e < 120;
 }
 
 // Resident CTAs per SM the register budget is fitted to (2, 3 or 4;
@@ -488,14 +555,23 @@ void launch_df_g(const StencilView& v, const StepArgs& a, int wc, double shift, 
                  cudaStream_t s) {
     static const int minb = [] {
         const char* e = getenv("CHEBFD_DF_FREE_CTAS");
-        return e ? std::min(4, std::max(2, atoi(e))) : 4;
+        return e ? std::min(4, std::max(2, atoi(e))) : 3;
     }();
-    if (minb == 4)
-        launch_df_gm<G, 4>(v, a, wc, shift, sms, s);
-    else if (minb == 3)
-        launch_df_gm<G, 3>(v, a, wc, shift, sms, s);
-    else
-        launch_df_gm<G, 2>(v, a, wc, shift, sms, s);
+    if (exact_hopping(v.hd)) {
+        if (minb == 4)
+            launch_df_gm<G, 4, true>(v, a, wc, shift, sms, s);
+        else if (minb == 3)
+            launch_df_gm<G, 3, true>(v, a, wc, shift, sms, s);
+        else
+            launch_df_gm<G, 2, true>(v, a, wc, shift, sms, s);
+    } else {
+        if (minb == 4)
+            launch_df_gm<G, 4, false>(v, a, wc, shift, sms, s);
+        else if (minb == 3)
+            launch_df_gm<G, 3, false>(v, a, wc, shift, sms, s);
+        else
+            launch_df_gm<G, 2, false>(v, a, wc, shift, sms, s);
+    }
 }
 
 StencilView view_of_gen(const Matrix& M) {
