@@ -123,6 +123,9 @@ void build_sell_from_device_csr(Matrix& M, const int64_t* d_rowptr, const int32_
 // shared bytes on the current device (occupancy API, cached per kernel); >= 1.
 int cached_occupancy(const void* kernel, int threads, size_t smem);
 
+// Keep the library's stream-ordered workspace cached between calls (oz_gram.cu).
+void cache_stream_workspace();
+
 // Blocked-ELL copy (bell_col, bell_val32) when the CSR has that shape; no-op otherwise.
 void build_bell(Matrix& M, const int64_t* d_rowptr, const int32_t* d_col, const double* d_val,
                 cudaStream_t stream);

@@ -183,6 +183,14 @@ __global__ void oz_colexp_kernel(const double* __restrict__ A, int64_t n, int co
     }
 }
 
+// Exact float of a small integer (|v| < 2^22) without a conversion
+// instruction: v added to the significand of 1.5 * 2^23, then 1.5 * 2^23
+// subtracted (both exact).  A 64-bit integer-to-float conversion would run on
+// the FP64 pipe, which is narrow on this part.
+__device__ __forceinline__ float oz_small_float(int v) {
+    return __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f);
+}
+
 // The 8 balanced base-128 digits of x / 2^(E - 1022) as a 56-bit fixed-point
 // number (E: the column's largest biased exponent field, so |x| < 2^(E-1022)).
 __device__ __forceinline__ void oz_digits(double x, int E, float* d) {
@@ -204,11 +212,11 @@ __device__ __forceinline__ void oz_digits(double x, int E, float* d) {
     if (bits >> 63) V = -V;
 #pragma unroll
     for (int s = OZ_SLICES - 1; s >= 1; --s) {
-        const long long dv = ((V & 127) ^ 64) - 64;   // in [-64, 63]
-        d[s] = (float)dv;
+        const int dv = (int)(((unsigned)V & 127u) ^ 64u) - 64;   // in [-64, 63]
+        d[s] = oz_small_float(dv);
         V = (V - dv) >> 7;
     }
-    d[0] = (float)V;                                  // in [-128, 128]
+    d[0] = oz_small_float((int)V);                    // in [-128, 128]
 }
 
 // S[s][c][k] (bf16, k contiguous, kpad rows per column) = digit s of A[k][c];
@@ -287,20 +295,44 @@ struct OzOut {
     int64_t ld;
     const int* ea;
     const int* eb;
+    bool accumulate;  // add to P (the row chunks of a long Gram) instead of writing it
 };
+
+// The tiles of a Gram A^T A that reach the diagonal or lie above it (the
+// rest are mirrored): row tile mi keeps the column tiles n0 >= m0 - (BN - 1),
+// i.e. nj >= mi * BM / BN.  Linear index t -> (mi, nj).
+__host__ __device__ inline int oz_upper_first(int mi) { return mi * (OZ_BM / OZ_BN); }
+__host__ __device__ inline int oz_upper_tiles(int tm, int tn) {
+    int c = 0;
+    for (int mi = 0; mi < tm; ++mi) c += tn > oz_upper_first(mi) ? tn - oz_upper_first(mi) : 0;
+    return c;
+}
 
 // One CTA: the 128 x 64 tile (m0, n0) of D = A_s B_s^T over the rows
 // [k_begin, k_end) of the K dimension (k_begin a multiple of OZ_CHUNK), A_s
-// and B_s the digit slices (rows x K, K contiguous).
+// and B_s the digit slices (rows x K, K contiguous).  upper_tn > 0: the grid's
+// x index runs over the upper tiles of a tm x upper_tn Gram (A == B).
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   int64_t rows_per_split, int64_t kpad, int64_t cols_a, int cols_b, OzOut o) {
+                   int64_t rows_per_split, int64_t kpad, int64_t cols_a, int cols_b, OzOut o,
+                   int upper_tn) {
     extern __shared__ unsigned char smem_raw[];
     OzSmem& sm = *reinterpret_cast<OzSmem*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t m0 = (int64_t)blockIdx.x * OZ_BM;
-    const int n0 = blockIdx.y * OZ_BN, split = blockIdx.z;
+    int mi = blockIdx.x, nj = blockIdx.y;
+    if (upper_tn > 0) {
+        int t = blockIdx.x;
+        mi = 0;
+        // every row tile of a square Gram keeps at least one tile; at most 16 row tiles
+        while (mi < 64 && t >= upper_tn - oz_upper_first(mi)) {
+            t -= upper_tn - oz_upper_first(mi);
+            ++mi;
+        }
+        nj = oz_upper_first(mi) + t;
+    }
+    const int64_t m0 = (int64_t)mi * OZ_BM;
+    const int n0 = nj * OZ_BN, split = blockIdx.z;
     const int64_t k_begin = split * rows_per_split;
     const int64_t k_end = min(kpad, k_begin + rows_per_split);
     const int nkb = (int)((k_end - k_begin) / OZ_BK);          // kpad is a multiple of OZ_BK
@@ -454,7 +486,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                         double v = ldexp((double)T[j], -28) + ldexp((double)t7[j], -35) +
                                    ldexp((double)t8[j], -42) + ldexp((double)t9[j], -49);
                         if (o.ea) v = ldexp(v, em + (o.eb[n] > 0 ? o.eb[n] - 1022 : 0));
-                        out[n] = v;
+                        out[n] = o.accumulate ? out[n] + v : v;
                     }
                 }
             }
@@ -470,13 +502,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 // over splits, the column scales 2^(E_a - 1022) 2^(E_b - 1022) 2^-14, and for
 // complex blocks the combination of the four real parts of each entry:
 //     C[p + q ldc] = sum_i A[i,p] conj(B[i,q]).
+// mirror: A == B and only the tiles on and above the diagonal were computed;
+// a real entry (r, c) with r > c is read at (c, r).
 __global__ void oz_finish_kernel(const double* __restrict__ P, int nsplit, int ca, int cb,
                                  int ma, int mb, bool cplx, const int* ea, const int* eb,
-                                 double* __restrict__ C, int ldc) {
+                                 double* __restrict__ C, int ldc, bool mirror) {
     const int total = ma * mb;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int p = t % ma, q = t / ma;
         auto g = [&](int r, int c) {
+            if (mirror && r > c) {
+                const int x = r;
+                r = c;
+                c = x;
+            }
             double s = 0.0;
             for (int k = 0; k < nsplit; ++k) s += P[((size_t)k * ca + r) * cb + c];
             const int e = (ea[r] > 0 ? ea[r] - 1022 : 0) + (eb[c] > 0 ? eb[c] - 1022 : 0) - 14;
@@ -549,12 +588,20 @@ struct OzBuf {
     OzBuf& operator=(const OzBuf&) = delete;
 };
 
-// Column exponents and digit slices of one real N x cols block.
-void oz_prepare(const double* A, int64_t n, int cols, int64_t ldr, int64_t kpad, int* emax,
-                __nv_bfloat16* S, int sms, cudaStream_t s) {
+// Column exponents (largest biased FP64 exponent field of each column) of one
+// real N x cols block, over all N rows.
+void oz_column_exponents(const double* A, int64_t n, int cols, int64_t ldr, int* emax, int sms,
+                         cudaStream_t s) {
     CHEBFD_CHECK_CUDA(cudaMemsetAsync(emax, 0, (size_t)cols * sizeof(int), s));
     const int g = (int)std::min<int64_t>((int64_t)sms * 8, std::max<int64_t>(1, n / 64));
     oz_colexp_kernel<<<g, 256, 0, s>>>(A, n, cols, ldr, emax);
+    CHEBFD_CHECK_CUDA(cudaGetLastError());
+}
+
+// Digit slices S[8][cols][kpad] of the rows [0, n) of a real block whose
+// column exponents are emax (rows n..kpad-1 zero).
+void oz_split_rows(const double* A, int64_t n, int cols, int64_t ldr, int64_t kpad,
+                   const int* emax, __nv_bfloat16* S, cudaStream_t s) {
     const dim3 grid((unsigned)(kpad / 64), (unsigned)((cols + 31) / 32));
     oz_split_kernel<<<grid, 256, 0, s>>>(A, n, cols, ldr, emax, kpad,
                                          reinterpret_cast<uint32_t*>(S));
@@ -643,37 +690,61 @@ void oz_prepare_rows(const double* A, int64_t rows, int kreal, int64_t ldr, int6
 
 size_t oz_gram_smem_bytes() { return sizeof(OzSmem) + 1024; }
 
+// Bytes of digit slices the tall products keep at a time: longer blocks are
+// processed in row chunks (a Gram keeps the column exponents of the whole
+// block, and split j of every chunk adds its partial into the same FP64
+// slot, chunk after chunk; the block product's rows are independent).
+constexpr int64_t OZ_WORKSPACE_BYTES = 2LL << 30;
+
 // C (ma x mb, column-major, ld ma) with C[p + q ma] = sum_i A[i,p] conj(B[i,q])
 // for row-major blocks A (N x ma, lda) and B (N x mb, ldb), FP64 real or
-// complex (interleaved); B == A (same shape) is recognised and split once.
-// Asynchronous on s; workspace from the stream-ordered allocator.
+// complex (interleaved); B == A (same shape) is recognised: split once, and
+// only the tiles on and above the diagonal computed.  Asynchronous on s;
+// workspace from the stream-ordered allocator.
 void oz_gram_rect(bool cplx, const double* A, int64_t lda, int ma, const double* B, int64_t ldb,
                   int mb, int64_t n, double* C, int sms, cudaStream_t s) {
+    cache_stream_workspace();
     const int ca = cplx ? 2 * ma : ma, cb = cplx ? 2 * mb : mb;
     const int64_t ldra = cplx ? 2 * lda : lda, ldrb = cplx ? 2 * ldb : ldb;
     CHEBFD_REQUIRE(ca >= 1 && cb >= 1 && ca <= 2048 && cb <= 2048, CHEBFD_EINVAL,
                    "Ozaki Gram: between 1 and 2048 real columns per operand");
     CHEBFD_REQUIRE(n >= 1, CHEBFD_EINVAL, "Ozaki Gram: empty block");
-    const int64_t kpad = (n + OZ_BK - 1) / OZ_BK * OZ_BK;
     const bool same = A == B && lda == ldb && ma == mb;
     OzBuf ea((size_t)ca * sizeof(int), s), eb(same ? 0 : (size_t)cb * sizeof(int), s);
-    OzBuf sa((size_t)OZ_SLICES * ca * kpad * sizeof(__nv_bfloat16), s);
-    OzBuf sb(same ? 0 : (size_t)OZ_SLICES * cb * kpad * sizeof(__nv_bfloat16), s);
-    oz_prepare(A, n, ca, ldra, kpad, (int*)ea.p, (__nv_bfloat16*)sa.p, sms, s);
-    if (!same) oz_prepare(B, n, cb, ldrb, kpad, (int*)eb.p, (__nv_bfloat16*)sb.p, sms, s);
+    oz_column_exponents(A, n, ca, ldra, (int*)ea.p, sms, s);
+    if (!same) oz_column_exponents(B, n, cb, ldrb, (int*)eb.p, sms, s);
     const int* eB = same ? (const int*)ea.p : (const int*)eb.p;
+    // rows per chunk: a multiple of OZ_CHUNK within the workspace
+    const int64_t slice_bytes_per_row = (int64_t)OZ_SLICES * (ca + (same ? 0 : cb)) * 2;
+    int64_t rows_c = std::max<int64_t>(
+        OZ_CHUNK, OZ_WORKSPACE_BYTES / slice_bytes_per_row / OZ_CHUNK * OZ_CHUNK);
+    if (rows_c >= n) rows_c = n;
+    const int64_t nchunk = (n + rows_c - 1) / rows_c;
+    const int64_t kpad_max = (rows_c + OZ_BK - 1) / OZ_BK * OZ_BK;
+    OzBuf sa((size_t)OZ_SLICES * ca * kpad_max * sizeof(__nv_bfloat16), s);
+    OzBuf sb(same ? 0 : (size_t)OZ_SLICES * cb * kpad_max * sizeof(__nv_bfloat16), s);
     const __nv_bfloat16* SB = same ? (const __nv_bfloat16*)sa.p : (const __nv_bfloat16*)sb.p;
-    const CUtensorMap tmA = slice_map((const __nv_bfloat16*)sa.p, kpad, ca, OZ_BM, 1);
-    const CUtensorMap tmB = slice_map(SB, kpad, cb, OZ_BN, OZ_SLICES);
-    // rows per CTA: a multiple of OZ_CHUNK, at most OZ_MAX_RANGE, enough
-    // splits that the tiles x splits fill the SMs
+    // K-splits of each chunk: rows per CTA a multiple of OZ_CHUNK, at most
+    // OZ_MAX_RANGE, enough splits that the tiles x splits fill the SMs
     const int tm = (ca + OZ_BM - 1) / OZ_BM, tn = (cb + OZ_BN - 1) / OZ_BN;
-    const int64_t chunks = (kpad + OZ_CHUNK - 1) / OZ_CHUNK;
-    int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(chunks, sms / std::max(1, tm * tn)));
-    int64_t range = (chunks + nsplit - 1) / nsplit * OZ_CHUNK;
-    if (range > OZ_MAX_RANGE) range = OZ_MAX_RANGE;
-    nsplit = (kpad + range - 1) / range;
-    OzBuf P((size_t)nsplit * ca * cb * sizeof(double), s);
+    const int tiles = same ? oz_upper_tiles(tm, tn) : tm * tn;
+    std::vector<int64_t> nsplit(nchunk), range(nchunk);
+    int64_t max_splits = 0;
+    for (int64_t c = 0; c < nchunk; ++c) {
+        const int64_t rows = std::min(rows_c, n - c * rows_c);
+        const int64_t kpad = (rows + OZ_BK - 1) / OZ_BK * OZ_BK;
+        const int64_t chunks = (kpad + OZ_CHUNK - 1) / OZ_CHUNK;
+        int64_t ns = std::max<int64_t>(1, std::min<int64_t>(chunks, sms / std::max(1, tiles)));
+        int64_t rg = (chunks + ns - 1) / ns * OZ_CHUNK;
+        if (rg > OZ_MAX_RANGE) rg = OZ_MAX_RANGE;
+        nsplit[c] = (kpad + rg - 1) / rg;
+        range[c] = rg;
+        max_splits = std::max(max_splits, nsplit[c]);
+    }
+    // split j of every chunk adds into P[j]; the chunks run in order on s
+    OzBuf P((size_t)max_splits * ca * cb * sizeof(double), s);
+    CHEBFD_CHECK_CUDA(
+        cudaMemsetAsync(P.p, 0, (size_t)max_splits * ca * cb * sizeof(double), s));
     const size_t smem = oz_gram_smem_bytes();
     static bool attr = false;
     if (!attr) {
@@ -682,13 +753,26 @@ void oz_gram_rect(bool cplx, const double* A, int64_t lda, int ma, const double*
                                                (int)smem));
         attr = true;
     }
-    const dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)nsplit);
-    const OzOut o{(double*)P.p, cb, nullptr, nullptr};
-    oz_gram_kernel<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, range, kpad, ca, cb, o);
-    CHEBFD_CHECK_CUDA(cudaGetLastError());
+    for (int64_t c = 0; c < nchunk; ++c) {
+        const int64_t r0 = c * rows_c, rows = std::min(rows_c, n - r0);
+        const int64_t kpad = (rows + OZ_BK - 1) / OZ_BK * OZ_BK;
+        oz_split_rows(A + r0 * ldra, rows, ca, ldra, kpad, (const int*)ea.p,
+                      (__nv_bfloat16*)sa.p, s);
+        if (!same)
+            oz_split_rows(B + r0 * ldrb, rows, cb, ldrb, kpad, eB, (__nv_bfloat16*)sb.p, s);
+        const CUtensorMap tmA = slice_map((const __nv_bfloat16*)sa.p, kpad, ca, OZ_BM, 1);
+        const CUtensorMap tmB = slice_map(SB, kpad, cb, OZ_BN, OZ_SLICES);
+        const dim3 grid = same ? dim3((unsigned)tiles, 1u, (unsigned)nsplit[c])
+                               : dim3((unsigned)tm, (unsigned)tn, (unsigned)nsplit[c]);
+        const OzOut o{(double*)P.p, cb, nullptr, nullptr, true};
+        oz_gram_kernel<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, range[c], kpad, ca, cb, o,
+                                                      same ? tn : 0);
+        CHEBFD_CHECK_CUDA(cudaGetLastError());
+    }
     const int total = ma * mb;
     oz_finish_kernel<<<std::min(4096, (total + 255) / 256), 256, 0, s>>>(
-        (const double*)P.p, (int)nsplit, ca, cb, ma, mb, cplx, (const int*)ea.p, eB, C, ma);
+        (const double*)P.p, (int)max_splits, ca, cb, ma, mb, cplx, (const int*)ea.p, eB, C, ma,
+        same);
     CHEBFD_CHECK_CUDA(cudaGetLastError());
 }
 
@@ -708,21 +792,24 @@ void oz_gemm(bool cplx, int r, int64_t n, int k, const double* M, int ldm, const
              int64_t ldy, double* T, int64_t ldt, int sms, cudaStream_t s, bool conj) {
     CHEBFD_REQUIRE(n >= 1 && k >= 1 && r >= 1, CHEBFD_EINVAL, "Ozaki block product: empty operand");
     CHEBFD_REQUIRE(n < (1LL << 31), CHEBFD_EINVAL, "Ozaki block product: N must be < 2^31");
+    cache_stream_workspace();
     const int kreal = cplx ? 2 * k : k, rows_b = cplx ? 2 * r : r;
     const int64_t kpad = (kreal + OZ_BK - 1) / OZ_BK * OZ_BK;
     const int64_t range = (kpad + OZ_CHUNK - 1) / OZ_CHUNK * OZ_CHUNK;
     CHEBFD_REQUIRE(range <= OZ_MAX_RANGE, CHEBFD_EINVAL, "Ozaki block product: k too large");
-    OzBuf ea((size_t)n * sizeof(int), s), eb((size_t)rows_b * sizeof(int), s);
-    OzBuf sa((size_t)OZ_SLICES * n * kpad * sizeof(__nv_bfloat16), s);
+    const int64_t ldry = cplx ? 2 * ldy : ldy, ldrt = cplx ? 2 * ldt : ldt;
+    // rows of Y per chunk: a multiple of OZ_BM within the workspace
+    int64_t rows_c = std::max<int64_t>(
+        OZ_BM, OZ_WORKSPACE_BYTES / ((int64_t)OZ_SLICES * kpad * 2) / OZ_BM * OZ_BM);
+    if (rows_c >= n) rows_c = n;
+    OzBuf ea((size_t)rows_c * sizeof(int), s), eb((size_t)rows_b * sizeof(int), s);
+    OzBuf sa((size_t)OZ_SLICES * rows_c * kpad * sizeof(__nv_bfloat16), s);
     OzBuf bh((size_t)rows_b * kreal * sizeof(double), s);
     OzBuf sb((size_t)OZ_SLICES * rows_b * kpad * sizeof(__nv_bfloat16), s);
-    oz_prepare_rows(Y, n, kreal, cplx ? 2 * ldy : ldy, kpad, (int*)ea.p, (__nv_bfloat16*)sa.p, sms,
-                    s);
     oz_build_b_kernel<<<std::min(1024, (k * r + 255) / 256), 256, 0, s>>>(M, ldm, k, r, cplx, conj,
                                                                           (double*)bh.p);
     oz_prepare_rows((const double*)bh.p, rows_b, kreal, kreal, kpad, (int*)eb.p,
                     (__nv_bfloat16*)sb.p, sms, s);
-    const CUtensorMap tmA = slice_map((const __nv_bfloat16*)sa.p, kpad, n, OZ_BM, 1);
     const CUtensorMap tmB = slice_map((const __nv_bfloat16*)sb.p, kpad, rows_b, OZ_BN, OZ_SLICES);
     const size_t smem = oz_gram_smem_bytes();
     static bool attr = false;
@@ -732,10 +819,32 @@ void oz_gemm(bool cplx, int r, int64_t n, int k, const double* M, int ldm, const
                                                (int)smem));
         attr = true;
     }
-    const dim3 grid((unsigned)((n + OZ_BM - 1) / OZ_BM), (unsigned)((rows_b + OZ_BN - 1) / OZ_BN), 1);
-    const OzOut o{T, cplx ? 2 * ldt : ldt, (const int*)ea.p, (const int*)eb.p};
-    oz_gram_kernel<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, range, kpad, n, rows_b, o);
-    CHEBFD_CHECK_CUDA(cudaGetLastError());
+    for (int64_t r0 = 0; r0 < n; r0 += rows_c) {
+        const int64_t rows = std::min(rows_c, n - r0);
+        oz_prepare_rows(Y + r0 * ldry, rows, kreal, ldry, kpad, (int*)ea.p, (__nv_bfloat16*)sa.p,
+                        sms, s);
+        const CUtensorMap tmA = slice_map((const __nv_bfloat16*)sa.p, kpad, rows, OZ_BM, 1);
+        const dim3 grid((unsigned)((rows + OZ_BM - 1) / OZ_BM),
+                        (unsigned)((rows_b + OZ_BN - 1) / OZ_BN), 1);
+        const OzOut o{T + r0 * ldrt, ldrt, (const int*)ea.p, (const int*)eb.p, false};
+        oz_gram_kernel<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, range, kpad, rows, rows_b, o, 0);
+        CHEBFD_CHECK_CUDA(cudaGetLastError());
+    }
+}
+
+// Up to 4 GiB of the stream-ordered pool stays cached across the stream
+// synchronisations of the solve (the default keeps none, so every call would
+// map its workspace again).  Once per device, for this process's default pool.
+void cache_stream_workspace() {
+    static std::once_flag once[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::call_once(once[dev], [dev] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+        uint64_t keep = 4ull << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    });
 }
 
 // CHEBFD_ETIMEOUT if an Ozaki Gram kernel gave up a bounded wait since the

@@ -176,3 +176,28 @@ def test_block_update_large_methods_agree(cplx):
     Tf = pkg.chebfd_block_update(Y, M, method="fp64").cpu().numpy()
     sc = np.abs(Y0) @ np.abs(M0)
     assert (np.abs(Tt - Tf) / sc).max() <= 1e-14
+
+
+def test_gram_and_block_update_in_row_chunks():
+    """Blocks long enough that the tensor-core path works in row chunks (2 GiB
+    of digit slices at a time: 65536 rows of 2048 real columns): a real
+    150001 x 2048 Gram (three chunks, the last ragged, their K-splits added in
+    place) and a complex 150001 x 1024 block times 1024 x 40 agree with cuBLAS
+    within 1e-13 of |A|^T |A| and |Y| |M|."""
+    n = 150001
+    g = torch.Generator(device=DEV).manual_seed(5)
+    A = torch.randn(n, 2048, dtype=torch.float64, device=DEV, generator=g)
+    A[:, 7] *= 2.0 ** 40                      # a column on another scale
+    Gt = pkg.chebfd_gram(A, method="tensor")
+    Gf = pkg.chebfd_gram(A, method="fp64")
+    sc = A.abs().T @ A.abs()
+    assert float(((Gt - Gf).abs() / sc).max()) <= 1e-13
+    assert torch.equal(Gt, Gt.T)               # mirrored: exactly symmetric
+    del A, Gt, Gf, sc
+    torch.cuda.empty_cache()
+    Y = torch.randn(n, 1024, dtype=torch.complex128, device=DEV, generator=g)
+    M = torch.randn(1024, 40, dtype=torch.complex128, device=DEV, generator=g)
+    Tt = pkg.chebfd_block_update(Y, M, method="tensor")
+    Tf = pkg.chebfd_block_update(Y, M, method="fp64")
+    sc = Y.abs() @ M.abs()
+    assert float(((Tt - Tf).abs() / sc).max()) <= 1e-13
