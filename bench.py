@@ -392,8 +392,13 @@ def fp64_class_kernels(pkg, H, N, alpha, beta, a, b, delta, peaks, stream):
 DENSE_PHASES = ("gram", "block_gemm", "eigensolve", "hy", "residuals", "other")
 
 
+LEARNED_FORMS = ("mlp", "mlp_matrix_free", "mlp_matrix_free_harmonic",
+                 "mlp_matrix_free_harmonic_inset")
+
+
 def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chiral=True,
-                precisions=("fp64", "mixed", "mixed_df"), matrix_free=False):
+                precisions=("fp64", "mixed", "mixed_df"), matrix_free=False,
+                learned_forms=LEARNED_FORMS):
     """Wall time of the whole ChebFD solve (Sec. 3.1 steps 4-8) to residual
     <= eps ||H|| for every accepted pair in [-delta, delta]: plain FP64 against
     the mixed forms (single-precision filter until the residuals stall, then
@@ -402,7 +407,9 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chir
     with `matrix_free` once more with H's entries rebuilt in registers in
     both the single-precision and the double-float steps, that once more
     with harmonic Ritz pairs for the window centre (Sec. 6), and that with
-    the filter window narrowed by half its half-width at half the degree."""
+    the filter window narrowed by half its half-width at half the degree.
+    A precision "mixed_df_matrix_free" is the heuristic-parameter MIXED_DF
+    form with the matrix-free steps; learned_forms picks the learned ones."""
     import torch
     out = {}
     lams = {}
@@ -436,14 +443,23 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chir
         if chiral and r["nev"]:
             # spec(H) = -spec(H) for the insulator: the window set is +- paired
             out[name]["chiral_pairing_error"] = float(np.abs(lam + lam[::-1]).max())
-        if name != "fp64" and "fp64" in lams and len(lam) == len(lams["fp64"]) and len(lam):
-            out[name]["max_eigenvalue_difference_vs_fp64"] = float(
-                np.abs(lam - lams["fp64"]).max())
-        if name != "fp64" and "fp64" in out:
-            out["speedup_%s_over_fp64" % name] = out["fp64"]["seconds"] / t
+        # against the first precision timed (the baseline: FP64 by default)
+        base = precisions[0] if precisions else None
+        if base and name != base and base in lams and len(lam) == len(lams[base]) and len(lam):
+            out[name]["max_eigenvalue_difference_vs_%s" % base] = float(
+                np.abs(lam - lams[base]).max())
+        if base and name != base and base in out:
+            out["speedup_%s_over_%s" % (name, base)] = out[base]["seconds"] / t
 
     for prec in precisions:
-        run(prec, ns, Np, "lanczos", prec)
+        if prec == "mixed_df_matrix_free":
+            H.set_matrix_free(True)
+            try:
+                run(prec, ns, Np, "lanczos", "mixed_df")
+            finally:
+                H.set_matrix_free(False)
+        else:
+            run(prec, ns, Np, "lanczos", prec)
     # learned parameters: (N_p, n_s, kernel) from the trained MLP on the KPM
     # features of this matrix and window (its time is part of the solve's)
     wpath = os.path.join(ROOT, "paper_1510_04895_gb300", "data", "mlp_weights.npy")
@@ -458,25 +474,29 @@ def bench_solve(pkg, H, a, b, delta, Np, ns, label, eps=1e-9, learned=True, chir
         t_choose = time.perf_counter() - t0
         extra = {"ns": ns_m, "Np": Np_m, "kernel": kern_m, "kpm_n_target": nt,
                  "seconds_parameter_choice": t_choose}
-        run("mixed_df_mlp", ns_m, Np_m, kern_m, "mixed_df", extra=extra, t_pre=t_choose)
+        if "mlp" in learned_forms:
+            run("mixed_df_mlp", ns_m, Np_m, kern_m, "mixed_df", extra=extra, t_pre=t_choose)
         if matrix_free:
             H.set_matrix_free(True)
             try:
-                run("mixed_df_mlp_matrix_free", ns_m, Np_m, kern_m, "mixed_df", extra=extra,
-                    t_pre=t_choose)
-                try:
-                    run("mixed_df_mlp_matrix_free_harmonic", ns_m, Np_m, kern_m, "mixed_df",
-                        extra=extra, t_pre=t_choose, extraction="harmonic")
-                except pkg.ChebFDError as e:     # reported; the other forms stand
-                    out["mixed_df_mlp_matrix_free_harmonic"] = {"error": str(e)}
+                if "mlp_matrix_free" in learned_forms:
+                    run("mixed_df_mlp_matrix_free", ns_m, Np_m, kern_m, "mixed_df", extra=extra,
+                        t_pre=t_choose)
+                if "mlp_matrix_free_harmonic" in learned_forms:
+                    try:
+                        run("mixed_df_mlp_matrix_free_harmonic", ns_m, Np_m, kern_m, "mixed_df",
+                            extra=extra, t_pre=t_choose, extraction="harmonic")
+                    except pkg.ChebFDError as e:     # reported; the other forms stand
+                        out["mixed_df_mlp_matrix_free_harmonic"] = {"error": str(e)}
                 # the window narrowed by half its half-width, half the degree
                 Np_i = max(8, int(round(0.5 * Np_m)))
-                try:
-                    run("mixed_df_mlp_matrix_free_harmonic_inset", ns_m, Np_i, kern_m,
-                        "mixed_df", extra=dict(extra, Np=Np_i, window_inset=0.5),
-                        t_pre=t_choose, extraction="harmonic", window_inset=0.5)
-                except pkg.ChebFDError as e:
-                    out["mixed_df_mlp_matrix_free_harmonic_inset"] = {"error": str(e)}
+                if "mlp_matrix_free_harmonic_inset" in learned_forms:
+                    try:
+                        run("mixed_df_mlp_matrix_free_harmonic_inset", ns_m, Np_i, kern_m,
+                            "mixed_df", extra=dict(extra, Np=Np_i, window_inset=0.5),
+                            t_pre=t_choose, extraction="harmonic", window_inset=0.5)
+                    except pkg.ChebFDError as e:
+                        out["mixed_df_mlp_matrix_free_harmonic_inset"] = {"error": str(e)}
             finally:
                 H.set_matrix_free(False)
     out["eps"] = eps
@@ -659,7 +679,8 @@ def run_ours(args):
                                                   learned=w["kind"] == "topi",
                                                   chiral=w["kind"] == "topi",
                                                   precisions=args.solve_precisions,
-                                                  matrix_free=w["kind"] == "topi")
+                                                  matrix_free=w["kind"] == "topi",
+                                                  learned_forms=args.solve_forms)
         except pkg.ChebFDError as e:     # reported, the throughput line still prints
             out["time_to_solution"] = {"error": str(e)}
 
@@ -766,6 +787,9 @@ def main():
     p.add_argument("--solve-precisions", dest="solve_precisions", nargs="*",
                    default=["fp64", "mixed", "mixed_df"],
                    help="precisions of the time-to-solution runs (the MLP run is extra)")
+    p.add_argument("--solve-forms", dest="solve_forms", nargs="*", default=list(LEARNED_FORMS),
+                   choices=list(LEARNED_FORMS),
+                   help="the learned-parameter solve forms to time")
     p.add_argument("--profile", choices=["step", "df", "solve", "pairs", "gram"], default=None,
                    help="run a short launch sequence for an ncu capture and exit")
     p.add_argument("--form", choices=["blocked", "sell", "free"], default="blocked",

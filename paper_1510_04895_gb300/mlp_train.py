@@ -1,12 +1,19 @@
 """Training records, training and evaluation of the parameter-predicting MLP.
 
-Records come from the method itself: small disordered insulators are solved
-by chebfd_solve with a grid of (N_p, n_s, kernel) around the paper's rule;
-each run's cost and convergence are recorded, and the cheapest run that found
-every eigenpair of the window is the label of that instance.
+Records come from the method itself: disordered insulators are solved by
+chebfd_solve with a grid of (N_p, n_s, kernel) around the paper's rule; each
+run's cost and convergence are recorded, and the cheapest run that found
+every eigenpair of the window is the label of that instance.  Four families
+(see instance()): small lattices (FP64 solves), and, solved with MIXED_DF,
+members of the disorder ensemble's kind with its fixed window and the two
+benchmark insulators' shapes reduced.  The committed records are
+data/mlp_records*.jsonl, the weights trained on all of them
+data/mlp_weights.npy.
 
-    python -m paper_1510_04895_gb300.mlp_train records --out R.jsonl --count 64 --first 0
-    python -m paper_1510_04895_gb300.mlp_train train --records R.jsonl --out W.npy
+    python -m paper_1510_04895_gb300.mlp_train records --family ensemble \
+        --precision mixed_df --count 64 --first 0 --out R.jsonl
+    python -m paper_1510_04895_gb300.mlp_train train --records R1.jsonl R2.jsonl --out W.npy
+    python -m paper_1510_04895_gb300.mlp_train evaluate --weights W.npy --family small
 
 Cost of a run, in products with H (the paper's N_MVM unit, Sec. 3.3) plus
 the dense work: N_iter n_s N_p + 3 N_iter n_s^2.  The factor 3 is the
@@ -32,15 +39,52 @@ NS_FACTORS = (2.0, 4.0, 6.0)
 KERNELS = ("jackson", "lanczos")
 
 
-def instance(k):
-    """Insulator k of the record set: edge L in {6, 7, 8}, Lz in {4..8},
-    W in U[0.3, 2.5], N_T in U{6..30}, from numpy's PCG64 seeded with 7000 + k."""
-    rs = np.random.default_rng(7000 + k)
-    L = int(rs.integers(6, 9))
-    Lz = int(rs.integers(4, 9))
-    W = float(rs.uniform(0.3, 2.5))
-    NT = int(rs.integers(6, 31))
-    return dict(k=k, L=L, Lz=Lz, W=W, NT=NT, seed=7000 + k)
+FAMILIES = ("small", "ensemble", "medium_shape", "large_shape")
+
+
+def instance(k, family="small"):
+    """Insulator k of a record family, from numpy's PCG64 seeded per family:
+    small         edge L in {6, 7, 8}, Lz in {4..8}, W in U[0.3, 2.5],
+                  N_T in U{6..30} (seed 7000 + k);
+    ensemble      members of the disorder ensemble's kind: cubes of edge
+                  L in {10, 11, 12}, W in U[0.2, 2.0], the fixed window
+                  [-0.05, 0.05] (N_T = 0: the window is not sized from a
+                  count; seed 20000 + k);
+    medium_shape  the 64x64x32 benchmark lattice's shape reduced: Lx = Ly =
+                  2 Lz with Lz in {5, 6, 7}, W = 1.0, N_T in U{10..60}
+                  (seed 30000 + k);
+    large_shape   the 200x200x100 lattice's shape reduced the same way,
+                  W = 0.5, N_T in U{10..60} (seed 40000 + k)."""
+    if family == "small":
+        rs = np.random.default_rng(7000 + k)
+        L = int(rs.integers(6, 9))
+        Lz = int(rs.integers(4, 9))
+        W = float(rs.uniform(0.3, 2.5))
+        NT = int(rs.integers(6, 31))
+        return dict(k=k, L=L, Lz=Lz, W=W, NT=NT, seed=7000 + k)
+    if family == "ensemble":
+        rs = np.random.default_rng(20000 + k)
+        L = int(rs.integers(10, 13))
+        return dict(k=k, family=family, L=L, Lz=L, W=float(rs.uniform(0.2, 2.0)), NT=0,
+                    delta=0.05, seed=20000 + k)
+    base = {"medium_shape": (30000, 1.0), "large_shape": (40000, 0.5)}[family]
+    rs = np.random.default_rng(base[0] + k)
+    Lz = int(rs.integers(5, 8))
+    return dict(k=k, family=family, L=2 * Lz, Lz=Lz, W=base[1], NT=int(rs.integers(10, 61)),
+                seed=base[0] + k)
+
+
+def window_of(inst, eigs):
+    """Half width of the instance's window: fixed, or sized to hold about N_T."""
+    return inst["delta"] if inst.get("delta") else window_for(eigs, inst["NT"])
+
+
+def dense_eigs(H):
+    """Eigenvalues of a (small) library matrix by dense diagonalisation on the
+    GPU (cuSOLVER through torch): the ground-truth window count of a record."""
+    import torch
+    A = torch.from_numpy(dense_of(H)).cuda()
+    return torch.linalg.eigvalsh(A).cpu().numpy()
 
 
 def cost_of(iterations, ns, Np):
@@ -71,19 +115,22 @@ def correct(r, exact, normH):
     return bool(np.abs(np.sort(r["lam"]) - exact).max() <= 1e-8 * normH)
 
 
-def make_records(count, first, out):
+def make_records(count, first, out, family="small", precision="fp64"):
     import torch
     import paper_1510_04895_gb300 as pkg
     torch.cuda.set_device(0)
     with open(out, "w") as f:
         for k in range(first, first + count):
-            inst = instance(k)
+            inst = instance(k, family)
             L, Lz, W = inst["L"], inst["Lz"], inst["W"]
             H = pkg.chebfd_matrix_create_lattice("topi", L, L, Lz, t=1.0, m=1.0, W=W,
                                                  seed=inst["seed"], also_single=True)
-            eigs = np.linalg.eigvalsh(dense_of(H))   # ground truth of the window count
-            delta = window_for(eigs, inst["NT"])
+            eigs = dense_eigs(H)                     # ground truth of the window count
+            delta = window_of(inst, eigs)
             exact = np.sort(eigs[np.abs(eigs) <= delta])
+            if len(exact) == 0:                      # a gapped member: nothing to learn
+                print("instance %d: empty window, skipped" % k, flush=True)
+                continue
             a, b, _, _ = pkg.chebfd_scale_bounds(H, 30, seed=0)
             normH = max(abs(a), abs(b))
             feats, nt_est = pkg.chebfd_param_features(H, -delta, delta, M_FEAT, a=a, b=b)
@@ -94,13 +141,15 @@ def make_records(count, first, out):
                     for kern in KERNELS:
                         Np = max(8, int(round(fp * Np_h)))
                         ns = max(16, int(np.ceil(fs * max(nt_est, 1.0) / 8.0)) * 8)
-                        r, sec = run_solve(pkg, H, -delta, delta, ns, Np, kern, a, b)
+                        r, sec = run_solve(pkg, H, -delta, delta, ns, Np, kern, a, b,
+                                           precision=precision)
                         ok = correct(r, exact, normH)
                         runs.append(dict(Np=Np, ns=ns, kernel=kern, converged=r["converged"],
                                          correct=ok, iterations=r["iterations"],
                                          n_mvm=r["n_mvm"], seconds=sec,
                                          cost=cost_of(r["iterations"], ns, Np)))
-            rec = dict(instance=inst, delta=delta, a=a, b=b, n_target_exact=len(exact),
+            rec = dict(instance=inst, precision=precision, delta=delta, a=a, b=b,
+                       n_target_exact=len(exact),
                        n_target_kpm=nt_est, features=[float(x) for x in feats],
                        heuristic=dict(ns=ns_h, Np=Np_h), runs=runs)
             f.write(json.dumps(rec) + "\n")
@@ -180,7 +229,7 @@ def train(records, hidden=128, steps=3000, lr=3e-3, seed=0):
     return net, losses
 
 
-def evaluate(weights, first, count, hidden=128):
+def evaluate(weights, first, count, hidden=128, family="small"):
     """Solve fresh instances with the paper's rule and with the MLP; returns
     per-instance dicts (cost, correctness, seconds) for both."""
     import torch
@@ -189,13 +238,15 @@ def evaluate(weights, first, count, hidden=128):
     net.set_params(np.asarray(weights, np.float32))
     out = []
     for k in range(first, first + count):
-        inst = instance(k)
+        inst = instance(k, family)
         L, Lz, W = inst["L"], inst["Lz"], inst["W"]
         H = pkg.chebfd_matrix_create_lattice("topi", L, L, Lz, t=1.0, m=1.0, W=W,
                                              seed=inst["seed"], also_single=True)
-        eigs = np.linalg.eigvalsh(dense_of(H))
-        delta = window_for(eigs, inst["NT"])
+        eigs = dense_eigs(H)
+        delta = window_of(inst, eigs)
         exact = np.sort(eigs[np.abs(eigs) <= delta])
+        if len(exact) == 0:
+            continue
         a, b, _, _ = pkg.chebfd_scale_bounds(H, 30, seed=0)
         normH = max(abs(a), abs(b))
         row = dict(instance=inst, n_target=len(exact))
@@ -217,24 +268,27 @@ def main():
     r.add_argument("--out", required=True)
     r.add_argument("--count", type=int, default=64)
     r.add_argument("--first", type=int, default=0)
+    r.add_argument("--family", default="small", choices=FAMILIES)
+    r.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed_df"])
     t = sub.add_parser("train")
-    t.add_argument("--records", required=True)
+    t.add_argument("--records", required=True, nargs="+")
     t.add_argument("--out", required=True)
     e = sub.add_parser("evaluate")
     e.add_argument("--weights", required=True)
     e.add_argument("--first", type=int, default=1000)
     e.add_argument("--count", type=int, default=16)
+    e.add_argument("--family", default="small", choices=FAMILIES)
     e.add_argument("--out", required=True)
     a = p.parse_args()
     if a.cmd == "records":
-        make_records(a.count, a.first, a.out)
+        make_records(a.count, a.first, a.out, a.family, a.precision)
     elif a.cmd == "train":
-        net, losses = train(load_records(a.records))
+        net, losses = train([rec for path in a.records for rec in load_records(path)])
         params, _ = net.get_params()
         np.save(a.out, params)
         print("losses", losses[::5], losses[-1])
     elif a.cmd == "evaluate":
-        rows = evaluate(np.load(a.weights), a.first, a.count)
+        rows = evaluate(np.load(a.weights), a.first, a.count, family=a.family)
         with open(a.out, "w") as f:
             for row in rows:
                 f.write(json.dumps(row) + "\n")
