@@ -91,6 +91,15 @@ def cost_of(iterations, ns, Np):
     return iterations * ns * Np + 3 * iterations * ns * ns
 
 
+def iteration_log(r):
+    """The solve's per-iteration records (chebfd_result_iterations): precision
+    phase, in-window / ghost / accepted counts, residual range and the seconds
+    of the filter and of the dense steps, kept with each training run."""
+    keys = ("fp64_filter", "in_window", "ghosts", "accepted", "res_min", "res_max", "Np",
+            "seconds_filter", "seconds_dense")
+    return [{k: rec[k] for k in keys} for rec in r["log"]]
+
+
 def window_for(H_dense_eigs, NT):
     """Half width of a symmetric window holding about NT eigenvalues of
     smallest |lambda|: the cut is placed in the widest gap of |lambda| among the
@@ -147,7 +156,8 @@ def make_records(count, first, out, family="small", precision="fp64"):
                         runs.append(dict(Np=Np, ns=ns, kernel=kern, converged=r["converged"],
                                          correct=ok, iterations=r["iterations"],
                                          n_mvm=r["n_mvm"], seconds=sec,
-                                         cost=cost_of(r["iterations"], ns, Np)))
+                                         cost=cost_of(r["iterations"], ns, Np),
+                                         log=iteration_log(r)))
             rec = dict(instance=inst, precision=precision, delta=delta, a=a, b=b,
                        n_target_exact=len(exact),
                        n_target_kpm=nt_est, features=[float(x) for x in feats],
@@ -256,7 +266,7 @@ def evaluate(weights, first, count, hidden=128, family="small"):
             r, sec = run_solve(pkg, H, -delta, delta, ns, Np, kern, a, b, max_iter=40)
             row[name] = dict(ns=ns, Np=Np, kernel=kern, iterations=r["iterations"],
                              correct=correct(r, exact, normH), seconds=sec,
-                             cost=cost_of(r["iterations"], ns, Np))
+                             cost=cost_of(r["iterations"], ns, Np), log=iteration_log(r))
         out.append(row)
     return out
 
