@@ -43,8 +43,8 @@ __device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 // keeping the values in registers).
 // ENS: an ensemble of such matrices (block-diagonal); each block row reads
 // its member's 2 alpha, g_n c_n and beta/alpha from the coefficient table.
-template <int G, bool ENS, int MINB>
-__global__ void __launch_bounds__(BELL_THREADS, MINB)
+template <int G, bool ENS>
+__global__ void __launch_bounds__(BELL_THREADS, 2)
     bell_step_kernel(BellView H, StepArgs a, int wc, float shift) {
     constexpr int B = kBellB, LB = kBellLB, SLOTS = BELL_THREADS / G, NV = LB * 8;
     constexpr unsigned FULL = 0xffffffffu;
@@ -170,24 +170,17 @@ __global__ void __launch_bounds__(BELL_THREADS, MINB)
     cp_async_wait_all();
 }
 
-// Resident CTAs per SM the registers are fitted to: 2 (128 registers), or 3
-// (80; CHEBFD_BELL_CTAS=3) for the single-matrix kernel; the ensemble kernel
-// keeps 2 (it spills at 80).
 template <int G, bool ENS>
 void launch_g(const BellView& v, const StepArgs& a, int wc, float shift, int sms,
               cudaStream_t s) {
     constexpr int SLOTS = BELL_THREADS / G;
     const size_t smem = (size_t)2 * SLOTS * kBellLB * 8 * sizeof(float4);
-    static const int ctas = [] {
-        const char* e = getenv("CHEBFD_BELL_CTAS");
-        return e && atoi(e) == 3 ? 3 : 2;
-    }();
-    auto kern = (!ENS && ctas == 3) ? bell_step_kernel<G, ENS, 3> : bell_step_kernel<G, ENS, 2>;
-    static bool attr[2] = {false, false};
-    if (!attr[ctas - 2]) {
+    auto kern = bell_step_kernel<G, ENS>;
+    static bool attr = false;
+    if (!attr) {
         CHEBFD_CHECK_CUDA(
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr[ctas - 2] = true;
+        attr = true;
     }
     const int grid = sms * std::min(8, cached_occupancy(reinterpret_cast<const void*>(kern),
                                                         BELL_THREADS, smem));
