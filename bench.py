@@ -643,23 +643,25 @@ def run_ours(args):
                                                   stream)
 
     # ---- end to end through the C ABI with host buffers ------------------------
+    # chebfd_filter_block_host: the page-locked host block is streamed through
+    # the device panel by panel (each panel copied in, filtered, copied back;
+    # the copies of neighbouring panels overlap the filter); the whole block
+    # crosses the link both ways every step
     Xh = torch.empty((N, ns), dtype=cdt, pin_memory=True)
     Xh.copy_(X)
-    Xd = torch.empty_like(X)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e_steps = max(1, min(args.steps, 3))
     for _ in range(e_steps):
-        Xd.copy_(Xh, non_blocking=True)
-        pkg.chebfd_filter_block(H, alpha, beta, gc, Xd)
-        Xh.copy_(Xd, non_blocking=True)
+        pkg.chebfd_filter_block_host(H, alpha, beta, gc, Xh)
         torch.cuda.synchronize()
     t_e2e = (time.perf_counter() - t0) / e_steps
     t_e2e = barrier_max(world, t_e2e)
     e2e = {"value": world * N * ns * Np / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": X.numel() * X.element_size(),
-           "d2h_bytes_per_step": X.numel() * X.element_size()}
-    del Xd, Xh
+           "d2h_bytes_per_step": X.numel() * X.element_size(),
+           "api": "chebfd_filter_block_host (page-locked host block, copies overlapped)"}
+    del Xh
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,

@@ -286,6 +286,26 @@ chebfd_status chebfd_filter_block_noalloc(const chebfd_matrix* H, double alpha, 
                                           const double* gc, int Np, void* X, int64_t ld, int nb,
                                           chebfd_dtype vdt, double* moments, void* stream);
 
+/* The filter of chebfd_filter_block (Sec. 2.1, Fig. ChebFD) for a block that
+ * lives in HOST memory: X_host (N x nb, row-major, ld >= nb elements per row,
+ * rows starting on 16-byte boundaries) is replaced by p[H] X_host.  The block
+ * is streamed through the device in panels of the filter's width (C128 32,
+ * C64 64, R64/R32 128 columns) with a ring of up to three device panels: the
+ * copy of panel p+1 to the device and of panel p-1 back to the host run on
+ * two library-owned copy streams while panel p is filtered on `stream`, so
+ * the transfers hide behind the filter.  The result equals chebfd_filter_block
+ * on a device copy of the block, bit for bit.  X_host should be page-locked
+ * (cudaHostAlloc / cudaHostRegister) for the copies to be asynchronous; it is
+ * read and written by the device until the work queued on `stream` by this
+ * call has completed, and the caller keeps ownership.  Device memory: three
+ * panels and two work panels, from the stream-ordered allocator.
+ * Errors: CHEBFD_EINVAL for a null or misaligned block, ld < nb, nb < 1,
+ * Np < 2 or a dtype that does not match the matrix.  Asynchronous on
+ * `stream`. */
+chebfd_status chebfd_filter_block_host(const chebfd_matrix* H, double alpha, double beta,
+                                       const double* gc, int Np, void* X_host, int64_t ld,
+                                       int nb, chebfd_dtype vdt, void* stream);
+
 /* One fused Chebyshev step (Sec. 2.1 recurrence, Fig. ChebFD; the kernel that
  * carries the filter): with U = T_{n-1}(A) X and W = T_{n-2}(A) X on entry,
  * W <- 2(alpha H + beta) U - W = T_n(A) X and Y <- Y + c W in one pass, for

@@ -11,5 +11,6 @@ from ._lib import (  # noqa: F401
     chebfd_rayleigh_ritz, chebfd_harmonic_ritz, chebfd_residuals, chebfd_scale_bounds,
     chebfd_solve, chebfd_spmv,
     chebfd_window_coeffs, lib, Ensemble, chebfd_ensemble_create, chebfd_ensemble_autotune,
-    chebfd_filter_block_noalloc, MLP, chebfd_param_features, chebfd_choose_params, pack_params,
+    chebfd_filter_block_noalloc, chebfd_filter_block_host, MLP, chebfd_param_features,
+    chebfd_choose_params, pack_params,
     unpack_params, chebfd_solve_batched, chebfd_gram, chebfd_block_update)

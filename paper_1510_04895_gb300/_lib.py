@@ -76,6 +76,9 @@ SIGNATURES = {
     "chebfd_filter_block_df": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double, c_dp,
                                               ctypes.c_int, c_vp, ctypes.c_int64, ctypes.c_int,
                                               ctypes.c_int, c_vp]),
+    "chebfd_filter_block_host": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double, c_dp,
+                                                ctypes.c_int, c_vp, ctypes.c_int64, ctypes.c_int,
+                                                ctypes.c_int, c_vp]),
     "chebfd_chebyshev_step": (ctypes.c_int, [c_vp, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, c_vp, c_vp, c_vp, ctypes.c_int64,
                                              ctypes.c_int, ctypes.c_int, c_vp]),
@@ -356,6 +359,27 @@ def chebfd_filter_block_noalloc(H, alpha, beta, gc, X, moments=None, stream=None
     _check(lib().chebfd_filter_block_noalloc(H.handle, alpha, beta, gc.ctypes.data_as(c_dp), Np,
                                              _ptr(X), X.stride(0), nb, dtype_of(X), mp,
                                              _stream(stream)), "chebfd_filter_block_noalloc")
+
+
+def chebfd_filter_block_host(H, alpha, beta, gc, X, stream=None):
+    """In place: X <- p[H] X for a HOST tensor or array X (N x nb, row-major;
+    page-locked for asynchronous copies), streamed through the device panel
+    by panel with the copies overlapping the filter.  Asynchronous on
+    `stream`: synchronise it before reading X."""
+    gc = np.ascontiguousarray(gc, np.float64)
+    Np = len(gc) - 1
+    n, nb = X.shape[0], X.shape[1]
+    if hasattr(X, "device"):
+        assert X.device.type == "cpu", "chebfd_filter_block_host takes a host block"
+        ld = X.stride(0)
+        dt = dtype_of(X)
+    else:
+        ld = X.strides[0] // X.itemsize
+        dt = {np.dtype(np.complex64): C64, np.dtype(np.complex128): C128,
+              np.dtype(np.float32): R32, np.dtype(np.float64): R64}[X.dtype]
+    _check(lib().chebfd_filter_block_host(H.handle, alpha, beta, gc.ctypes.data_as(c_dp), Np,
+                                          _ptr(X), ld, nb, dt, _stream(stream)),
+           "chebfd_filter_block_host")
 
 
 def chebfd_filter_block_df(H, alpha, beta, gc, X, stream=None):

@@ -15,6 +15,8 @@ namespace chebfd {
 void filter_block_impl(const Matrix& M, double alpha, double beta, const double* gc, int Np,
                        void* X, int64_t ld, int nb, chebfd_dtype dt, double* moments,
                        cudaStream_t s, int panel = 0);
+void filter_block_host_impl(const Matrix& M, double alpha, double beta, const double* gc, int Np,
+                            void* Xh, int64_t ld, int nb, chebfd_dtype dt, cudaStream_t s);
 void spmv_impl(const Matrix& M, double alpha, double beta, const void* X, void* Y, int64_t ld,
                int nb, chebfd_dtype dt, cudaStream_t s);
 void kpm_impl(const Matrix& M, double alpha, double beta, int Mm, int R, uint64_t seed,
@@ -629,6 +631,16 @@ chebfd_status chebfd_filter_block(const chebfd_matrix* H, double alpha, double b
         CHEBFD_REQUIRE(H, CHEBFD_EINVAL, "null matrix");
         filter_block_impl(H->m, alpha, beta, gc, Np, X, ld, nb, vdt, moments,
                           as_stream(stream));
+    });
+}
+
+chebfd_status chebfd_filter_block_host(const chebfd_matrix* H, double alpha, double beta,
+                                       const double* gc, int Np, void* X_host, int64_t ld,
+                                       int nb, chebfd_dtype vdt, void* stream) {
+    return guarded([&] {
+        CHEBFD_REQUIRE(H, CHEBFD_EINVAL, "null matrix");
+        filter_block_host_impl(H->m, alpha, beta, gc, Np, X_host, ld, nb, vdt,
+                               as_stream(stream));
     });
 }
 

@@ -378,6 +378,90 @@ void filter_block_impl(const Matrix& M, double alpha, double beta, const double*
     }
 }
 
+namespace {
+
+// The two copy streams of a device (to and from the host), created once.
+struct CopyStreams {
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+};
+
+CopyStreams& copy_streams() {
+    static std::once_flag once[64];
+    static CopyStreams cs[64];
+    int dev = 0;
+    CHEBFD_CHECK_CUDA(cudaGetDevice(&dev));
+    CHEBFD_REQUIRE(dev >= 0 && dev < 64, CHEBFD_ECUDA, "device index out of range");
+    std::call_once(once[dev], [dev] {
+        CHEBFD_CHECK_CUDA(cudaStreamCreateWithFlags(&cs[dev].h2d, cudaStreamNonBlocking));
+        CHEBFD_CHECK_CUDA(cudaStreamCreateWithFlags(&cs[dev].d2h, cudaStreamNonBlocking));
+    });
+    return cs[dev];
+}
+
+// Events owned for the length of one call (destroyed when it returns; the
+// runtime releases an event still pending once it completes).
+struct EventSet {
+    std::vector<cudaEvent_t> e;
+    void create(int n) {
+        e.assign(n, nullptr);
+        for (auto& x : e) CHEBFD_CHECK_CUDA(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+    }
+    ~EventSet() {
+        for (auto x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
+}  // namespace
+
+// The filter of a host-resident block, streamed through the device panel by
+// panel (same panels and kernels as filter_block_impl, so the same result):
+// a ring of up to three device panels; panel p is copied in on the h2d
+// stream, filtered on s, copied back on the d2h stream, and its buffer is
+// refilled (panel p + 3) only after that copy-out has completed.
+void filter_block_host_impl(const Matrix& M, double alpha, double beta, const double* gc, int Np,
+                            void* Xh, int64_t ld, int nb, chebfd_dtype dt, cudaStream_t s) {
+    validate_block(M, dt, Xh, ld, nb);
+    CHEBFD_REQUIRE(gc != nullptr && Np >= 2, CHEBFD_EINVAL, "need Np >= 2 and coefficients");
+    CHEBFD_REQUIRE(std::isfinite(alpha) && std::isfinite(beta), CHEBFD_EINVAL,
+                   "alpha, beta must be finite");
+    const int pw = max_panel_width(dt);
+    const int np = (nb + pw - 1) / pw, nbuf = std::min(np, 3);
+    const int64_t ldp = padded_ld(dt, std::min(pw, nb));
+    const size_t es = dtype_size(dt), panel_bytes = (size_t)M.n * ldp * es;
+    DeviceBuffer P(panel_bytes * nbuf, s), U(panel_bytes, s), W(panel_bytes, s);
+    CopyStreams& cs = copy_streams();
+    EventSet ev;
+    ev.create(1 + 3 * np);
+    auto h2d_done = [&](int p) { return ev.e[1 + 3 * p]; };
+    auto filtered = [&](int p) { return ev.e[2 + 3 * p]; };
+    auto d2h_done = [&](int p) { return ev.e[3 + 3 * p]; };
+    // the copy streams start after the allocations and earlier work on s
+    CHEBFD_CHECK_CUDA(cudaEventRecord(ev.e[0], s));
+    CHEBFD_CHECK_CUDA(cudaStreamWaitEvent(cs.h2d, ev.e[0], 0));
+    CHEBFD_CHECK_CUDA(cudaStreamWaitEvent(cs.d2h, ev.e[0], 0));
+    for (int p = 0; p < np; ++p) {
+        const int p0 = p * pw, pnb = std::min(pw, nb - p0);
+        char* buf = (char*)P.p + (size_t)(p % nbuf) * panel_bytes;
+        char* host = (char*)Xh + (size_t)p0 * es;
+        if (p >= nbuf) CHEBFD_CHECK_CUDA(cudaStreamWaitEvent(cs.h2d, d2h_done(p - nbuf), 0));
+        CHEBFD_CHECK_CUDA(cudaMemcpy2DAsync(buf, ldp * es, host, ld * es, pnb * es, M.n,
+                                            cudaMemcpyHostToDevice, cs.h2d));
+        CHEBFD_CHECK_CUDA(cudaEventRecord(h2d_done(p), cs.h2d));
+        CHEBFD_CHECK_CUDA(cudaStreamWaitEvent(s, h2d_done(p), 0));
+        filter_panel(M, alpha, beta, gc, Np, buf, ldp, pnb, dt, nullptr, 0, (char*)U.p,
+                     (char*)W.p, ldp, nullptr, nullptr, s, nullptr, nullptr);
+        CHEBFD_CHECK_CUDA(cudaEventRecord(filtered(p), s));
+        CHEBFD_CHECK_CUDA(cudaStreamWaitEvent(cs.d2h, filtered(p), 0));
+        CHEBFD_CHECK_CUDA(cudaMemcpy2DAsync(host, ld * es, buf, ldp * es, pnb * es, M.n,
+                                            cudaMemcpyDeviceToHost, cs.d2h));
+        CHEBFD_CHECK_CUDA(cudaEventRecord(d2h_done(p), cs.d2h));
+    }
+    // the caller's stream (and the panel buffers' release on it) waits for
+    // the last copy-out, which follows every earlier one on the d2h stream
+    CHEBFD_CHECK_CUDA(cudaStreamWaitEvent(s, d2h_done(np - 1), 0));
+}
+
 void spmv_impl(const Matrix& M, double alpha, double beta, const void* X, void* Y, int64_t ld,
                int nb, chebfd_dtype dt, cudaStream_t s) {
     validate_block(M, dt, X, ld, nb);

@@ -247,3 +247,44 @@ def test_kpm_moments_match_oracle():
     mu = pkg.chebfd_kpm_moments(H, alpha, beta, 64, 8, seed=3)
     ref = okpm.moments(Ho, alpha, beta, 64, 8, seed=3, complex_values=True)
     assert np.abs(mu - ref).max() <= 1e-12
+
+
+@pytest.mark.parametrize("dtype,nb", [(torch.complex64, 200), (torch.complex128, 72),
+                                      (torch.float32, 136), (torch.float64, 8)])
+def test_host_block_filter_equals_device_filter(dtype, nb):
+    """chebfd_filter_block_host streams a host block through the device panel
+    by panel (ring of three device panels, copies on two streams overlapping
+    the filter): bit-identical to chebfd_filter_block on a device copy, with
+    more panels than ring slots, a ragged last panel and a padded host row
+    stride; a page-locked and a pageable host block."""
+    cplx = dtype.is_complex
+    H = (pkg.chebfd_matrix_create_lattice("topi", 6, 5, 7, t=1.0, m=1.0, W=1.0, seed=3,
+                                          also_single=True) if cplx else
+         pkg.chebfd_matrix_create_lattice("graphene", 20, 17, 1, t=1.0, W=1.0, seed=2,
+                                          also_single=True))
+    gc = pkg.chebfd_window_coeffs(-4.5, 4.5, -0.2, 0.3, 40, "lanczos", 2.0)
+    ld = nb + (8 if dtype in (torch.complex64, torch.float32) else 2)  # 16-byte rows, padded
+    X0 = workloads.random_block(9, H.n, ld, cplx)
+    Xd = torch.from_numpy(X0).to(dtype).to(DEV)
+    pkg.chebfd_filter_block(H, 0.21, 0.0, gc, Xd[:, :nb])
+    ref = Xd.cpu()
+    for pinned in (True, False):
+        Xh = torch.from_numpy(X0).to(dtype)
+        if pinned:
+            Xh = Xh.pin_memory()
+        pkg.chebfd_filter_block_host(H, 0.21, 0.0, gc, Xh[:, :nb])
+        torch.cuda.synchronize()
+        assert torch.equal(Xh[:, :nb], ref[:, :nb])
+        assert torch.equal(Xh[:, nb:], torch.from_numpy(X0).to(dtype)[:, nb:])  # padding untouched
+
+
+def test_host_block_filter_rejects_bad_blocks():
+    H = pkg.chebfd_matrix_create_lattice("topi", 3, 3, 3, W=0.5, seed=0, also_single=True)
+    gc = np.ones(5)
+    Xh = torch.zeros((H.n, 6), dtype=torch.complex64)       # 48-byte rows: fine
+    with pytest.raises(pkg.ChebFDError):
+        pkg.chebfd_filter_block_host(H, 0.2, 0.0, gc, Xh[:, :3])   # 24 bytes per row
+    with pytest.raises(pkg.ChebFDError):
+        pkg.chebfd_filter_block_host(H, 0.2, 0.0, gc[:2], Xh)     # N_p < 2
+    with pytest.raises(pkg.ChebFDError):
+        pkg.chebfd_filter_block_host(H, 0.2, 0.0, gc, torch.zeros((H.n, 8)))  # real vs complex
