@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -298,6 +299,12 @@ struct OzOut {
     bool accumulate;  // add to P (the row chunks of a long Gram) instead of writing it
 };
 
+// v * 2^e: one exact multiplication when 2^e is a normal double, else ldexp.
+__device__ __forceinline__ double oz_scale(double v, int e) {
+    if (e >= -1022 && e <= 1023) return v * __longlong_as_double((long long)(e + 1023) << 52);
+    return ldexp(v, e);
+}
+
 // The tiles of a Gram A^T A that reach the diagonal or lie above it (the
 // rest are mirrored): row tile mi keeps the column tiles n0 >= m0 - (BN - 1),
 // i.e. nj >= mi * BM / BN.  Linear index t -> (mi, nj).
@@ -311,7 +318,8 @@ __host__ __device__ inline int oz_upper_tiles(int tm, int tn) {
 // One CTA: the 128 x 64 tile (m0, n0) of D = A_s B_s^T over the rows
 // [k_begin, k_end) of the K dimension (k_begin a multiple of OZ_CHUNK), A_s
 // and B_s the digit slices (rows x K, K contiguous).  upper_tn > 0: the grid's
-// x index runs over the upper tiles of a tm x upper_tn Gram (A == B).
+// x index runs over the upper tiles of a tm x upper_tn Gram (A == B);
+// upper_tn < 0: x is the column tile and y the row tile.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    int64_t rows_per_split, int64_t kpad, int64_t cols_a, int cols_b, OzOut o,
@@ -321,7 +329,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     int mi = blockIdx.x, nj = blockIdx.y;
-    if (upper_tn > 0) {
+    if (upper_tn < 0) {  // the block product: the column tiles of one row tile run together
+        mi = blockIdx.y;
+        nj = blockIdx.x;
+    } else if (upper_tn > 0) {
         int t = blockIdx.x;
         mi = 0;
         // every row tile of a square Gram keeps at least one tile; at most 16 row tiles
@@ -483,9 +494,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 for (int j = 0; j < 32; ++j) {
                     const int n = n0 + 32 * half + j;
                     if (n < cols_b) {
-                        double v = ldexp((double)T[j], -28) + ldexp((double)t7[j], -35) +
-                                   ldexp((double)t8[j], -42) + ldexp((double)t9[j], -49);
-                        if (o.ea) v = ldexp(v, em + (o.eb[n] > 0 ? o.eb[n] - 1022 : 0));
+                        // the power-of-two weights folded into FMAs; groups 8 and 9
+                        // (2^-7 and 2^-14 below group 7) combined in FP32: the FP64
+                        // pipe, narrow on this part, does 6 operations per entry
+                        const float t89 = fmaf(t9[j], 0x1p-7f, t8[j]);
+                        double v = fma((double)t7[j], 0x1p-35,
+                                       fma((double)t89, 0x1p-42, (double)T[j] * 0x1p-28));
+                        if (o.ea) v = oz_scale(v, em + (o.eb[n] > 0 ? o.eb[n] - 1022 : 0));
                         out[n] = o.accumulate ? out[n] + v : v;
                     }
                 }
@@ -824,10 +839,13 @@ void oz_gemm(bool cplx, int r, int64_t n, int k, const double* M, int ldm, const
         oz_prepare_rows(Y + r0 * ldry, rows, kreal, ldry, kpad, (int*)ea.p, (__nv_bfloat16*)sa.p,
                         sms, s);
         const CUtensorMap tmA = slice_map((const __nv_bfloat16*)sa.p, kpad, rows, OZ_BM, 1);
-        const dim3 grid((unsigned)((rows + OZ_BM - 1) / OZ_BM),
-                        (unsigned)((rows_b + OZ_BN - 1) / OZ_BN), 1);
+        // x: the column tiles of one row tile, consecutive, so they share its
+        // A slices in L2
+        const unsigned tm = (unsigned)((rows + OZ_BM - 1) / OZ_BM);
+        const unsigned tn = (unsigned)((rows_b + OZ_BN - 1) / OZ_BN);
         const OzOut o{T + r0 * ldrt, ldrt, (const int*)ea.p, (const int*)eb.p, false};
-        oz_gram_kernel<<<grid, OZ_THREADS, smem, s>>>(tmA, tmB, range, kpad, rows, rows_b, o, 0);
+        oz_gram_kernel<<<dim3(tn, tm, 1), OZ_THREADS, smem, s>>>(tmA, tmB, range, kpad, rows,
+                                                                 rows_b, o, -1);
         CHEBFD_CHECK_CUDA(cudaGetLastError());
     }
 }
