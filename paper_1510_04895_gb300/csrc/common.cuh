@@ -123,6 +123,10 @@ void build_sell_from_device_csr(Matrix& M, const int64_t* d_rowptr, const int32_
 // shared bytes on the current device (occupancy API, cached per kernel); >= 1.
 int cached_occupancy(const void* kernel, int threads, size_t smem);
 
+// The kernel may use `bytes` of dynamic shared memory on the current device
+// (cudaFuncSetAttribute once per device and kernel; thread-safe).
+void ensure_dynamic_smem(const void* kernel, size_t bytes);
+
 // Keep the library's stream-ordered workspace cached between calls (oz_gram.cu).
 void cache_stream_workspace();
 

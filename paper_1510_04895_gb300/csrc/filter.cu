@@ -63,6 +63,19 @@ int cached_occupancy(const void* kernel, int threads, size_t smem) {
     return occ;
 }
 
+void ensure_dynamic_smem(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*>, size_t> set_to;
+    int dev = 0;
+    CHEBFD_CHECK_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& have = set_to[std::make_tuple(dev, kernel)];
+    if (bytes <= have) return;
+    CHEBFD_CHECK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)bytes));
+    have = bytes;
+}
+
 SiteOrder site_order_of(const Matrix& M, int wc) {
     SiteOrder o{};
     if (!M.has_gen || M.gen.kind == CHEBFD_LATTICE_GRAPHENE || !M.identity_perm) return o;

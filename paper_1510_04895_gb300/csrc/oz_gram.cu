@@ -761,13 +761,7 @@ void oz_gram_rect(bool cplx, const double* A, int64_t lda, int ma, const double*
     CHEBFD_CHECK_CUDA(
         cudaMemsetAsync(P.p, 0, (size_t)max_splits * ca * cb * sizeof(double), s));
     const size_t smem = oz_gram_smem_bytes();
-    static bool attr = false;
-    if (!attr) {
-        CHEBFD_CHECK_CUDA(cudaFuncSetAttribute(oz_gram_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem));
-        attr = true;
-    }
+    ensure_dynamic_smem(reinterpret_cast<const void*>(oz_gram_kernel), smem);
     for (int64_t c = 0; c < nchunk; ++c) {
         const int64_t r0 = c * rows_c, rows = std::min(rows_c, n - r0);
         const int64_t kpad = (rows + OZ_BK - 1) / OZ_BK * OZ_BK;
@@ -827,13 +821,7 @@ void oz_gemm(bool cplx, int r, int64_t n, int k, const double* M, int ldm, const
                     (__nv_bfloat16*)sb.p, sms, s);
     const CUtensorMap tmB = slice_map((const __nv_bfloat16*)sb.p, kpad, rows_b, OZ_BN, OZ_SLICES);
     const size_t smem = oz_gram_smem_bytes();
-    static bool attr = false;
-    if (!attr) {
-        CHEBFD_CHECK_CUDA(cudaFuncSetAttribute(oz_gram_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem));
-        attr = true;
-    }
+    ensure_dynamic_smem(reinterpret_cast<const void*>(oz_gram_kernel), smem);
     for (int64_t r0 = 0; r0 < n; r0 += rows_c) {
         const int64_t rows = std::min(rows_c, n - r0);
         oz_prepare_rows(Y + r0 * ldry, rows, kreal, ldry, kpad, (int*)ea.p, (__nv_bfloat16*)sa.p,

@@ -625,13 +625,7 @@ void launch_stencil2(const Matrix& M, const void* u0, const void* um, void* u1, 
     a.c1 = (float)c1;
     a.c2 = (float)c2;
     a.Z = s2_planes(v.Lz);
-    static bool attr = false;
-    if (!attr) {
-        CHEBFD_CHECK_CUDA(cudaFuncSetAttribute(stencil2_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)S2_RING_BYTES));
-        attr = true;
-    }
+    ensure_dynamic_smem(reinterpret_cast<const void*>(stencil2_kernel), S2_RING_BYTES);
     const int grid = (int)((v.Lx / S2_TX) * (v.Ly / S2_TY) * (v.Lz / a.Z));
     stencil2_kernel<<<grid, S2_THREADS, S2_RING_BYTES, s>>>(v, a);
     CHEBFD_CHECK_CUDA(cudaGetLastError());

@@ -176,12 +176,7 @@ void launch_g(const BellView& v, const StepArgs& a, int wc, float shift, int sms
     constexpr int SLOTS = BELL_THREADS / G;
     const size_t smem = (size_t)2 * SLOTS * kBellLB * 8 * sizeof(float4);
     auto kern = bell_step_kernel<G, ENS>;
-    static bool attr = false;
-    if (!attr) {
-        CHEBFD_CHECK_CUDA(
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    ensure_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
     const int grid = sms * std::min(8, cached_occupancy(reinterpret_cast<const void*>(kern),
                                                         BELL_THREADS, smem));
     kern<<<grid, BELL_THREADS, smem, s>>>(v, a, wc, shift);
