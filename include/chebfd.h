@@ -26,6 +26,12 @@
  *  - Scalars: chebfd_dtype names the element type of vectors and matrix
  *    values.  A complex H (insulator) takes C128/C64 vectors, a real H
  *    (graphene, diagonal) takes R64/R32 vectors.
+ *  - Workspace comes from the CUDA stream-ordered allocator (the device's
+ *    default memory pool).  The first call that uses the tensor-core dense
+ *    products sets that pool's release threshold to 4 GiB for the rest of
+ *    the process, so up to 4 GiB of freed workspace stays reserved across
+ *    stream synchronisations instead of being mapped again on every call;
+ *    a process-local setting of the pool, not of the GPU.
  */
 #ifndef CHEBFD_H
 #define CHEBFD_H
