@@ -121,3 +121,37 @@ def test_full_ensemble_sampled_members():
         ref = ofilt.filter_block(Ho, al[i], be[i], gcs[i], xin)
         tol = Np * 30 * 2.0 ** -24 * np.linalg.norm(xin) / np.linalg.norm(ref)
         assert rel(got[r0:r1], ref) <= tol, i
+
+
+def test_medium_insulator_host_block_filter_full_size():
+    """The benchmark's end-to-end path at its full size: the 64x64x32x4
+    insulator (N = 524288), the 256-column complex64 search block in
+    page-locked host memory (1.07 GB), N_p = 8, streamed through the device by
+    chebfd_filter_block_host (four 64-column panels through a ring of three):
+    bit-identical to chebfd_filter_block on a device copy, and within
+    complex64 rounding of the oracle on 64 sampled rows."""
+    w = workloads.TOPI_MEDIUM
+    H = pkg.chebfd_matrix_create_lattice("topi", w["Lx"], w["Ly"], w["Lz"], t=w["t"], m=w["m"],
+                                         W=w["W"], seed=w["seed"], also_single=True)
+    a, b = -4.2, 4.2
+    alpha, beta = coeffs.scaling(a, b)
+    gc = pkg.chebfd_window_coeffs(a, b, -0.14, 0.14, 8, "lanczos", 2.0)
+    Xd = torch.empty((H.n, 256), dtype=torch.complex64, device=DEV)
+    pkg.chebfd_random_block(Xd, ns_total=256, seed=3)
+    X0 = Xd.cpu()
+    Xh = X0.clone().pin_memory()
+    pkg.chebfd_filter_block(H, alpha, beta, gc, Xd)
+    pkg.chebfd_filter_block_host(H, alpha, beta, gc, Xh)
+    torch.cuda.synchronize()
+    assert torch.equal(Xh, Xd.cpu())
+    # sampled rows against the oracle's filter (FP64 on the same inputs)
+    rs = np.random.default_rng(8)
+    sites = np.unique(np.concatenate([[0, H.n // 4 - 1], rs.integers(0, H.n // 4, 14)]))
+    rows = (4 * sites[:, None] + np.arange(4)[None, :]).reshape(-1)
+    Ho = lattice.to_scipy(*lattice.topi_csr(w["Lx"], w["Ly"], w["Lz"], t=w["t"], m=w["m"],
+                                            W=w["W"], seed=w["seed"]))
+    ref = ofilt.filter_block(Ho, alpha, beta, coeffs.filter_coeffs(a, b, -0.14, 0.14, 8,
+                                                                    "lanczos", 2.0),
+                             X0.numpy()[:, :8].astype(np.complex128))
+    got = Xh.numpy()[rows, :8].astype(np.complex128)
+    assert np.abs(got - ref[rows]).max() <= 1e-4 * np.abs(ref).max()
