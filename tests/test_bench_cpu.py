@@ -100,6 +100,7 @@ def test_solve_forms_of_the_benchmark(monkeypatch, fail):
     failing harmonic form is reported without losing the others."""
     import torch
     monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
+    monkeypatch.setattr(bench, "warm_up_solves", lambda pkg: None)
     fake = _FakeLib(fail)
     H = fake
     out = bench.bench_solve(fake, H, -4.2, 4.2, 0.14, 309, 256, "fake", precisions=("fp64",),
@@ -122,3 +123,22 @@ def test_solve_forms_of_the_benchmark(monkeypatch, fail):
                 "mixed_df_mlp_matrix_free_harmonic")
         assert out[name] == {"error": "planted failure"}
         assert out["mixed_df_mlp_matrix_free"]["converged"]
+
+
+def test_solves_are_warmed_up_outside_the_timed_region():
+    """Every precision and extraction is run once, stored-matrix and
+    matrix-free, on a small insulator before the timed solves."""
+    fake = _FakeLib()
+    made = []
+
+    def create(kind, Lx, Ly, Lz, **kw):
+        made.append((kind, Lx, Ly, Lz, kw.get("also_single")))
+        return fake
+    fake.chebfd_matrix_create_lattice = create
+    bench.warm_up_solves(fake)
+    assert made == [("topi", 8, 8, 8, True)]
+    solves = [(c["precision"], c["extraction"]) for c in fake.calls if "Np" in c]
+    assert sorted(solves) == sorted([(p, e) for p in ("fp64", "mixed", "mixed_df")
+                                     for e in ("ritz", "harmonic")] * 2)
+    assert [c for c in fake.calls if "matrix_free" in c] == [dict(matrix_free=False),
+                                                             dict(matrix_free=True)]
