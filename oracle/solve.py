@@ -88,6 +88,18 @@ def degree_from_moments(mu, D, a, b, lam_lo, lam_hi, ns, Np0, M_max=1024):
     return NT, dprime, int(min(max(Np, max(2, Np0 // 4)), 4 * Np0))
 
 
+def deflate(Y, L):
+    """Y - L (L^H Y): the block with the span of the locked vectors removed
+    (hard locking, Sec. 6; L orthonormal)."""
+    return Y - L @ (L.conj().T @ Y)
+
+
+def converging(res, res_prev_nearest):
+    """A pair still converging for the empty-window test (reading of Sec. 3.1
+    step 8): its residual at most 0.9 of the previous iteration's nearest."""
+    return res <= 0.9 * res_prev_nearest
+
+
 def search_vectors(seed, D, ns, complex_values):
     idx = np.arange(D, dtype=np.uint64)[:, None] * np.uint64(ns) + np.arange(ns, dtype=np.uint64)[None, :]
     if complex_values:
@@ -133,11 +145,11 @@ def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
         if adaptive and it == 1:
             gc = coeffs.filter_coeffs(a, b, c - d, c + d, adapted[2], kind, mu)
         for _ in range(2 if L.shape[1] else 0):
-            Y = Y - L @ (L.conj().T @ Y)
+            Y = deflate(Y, L)
         Q, rank, refill = svqb.svqb(Y, seed=seed, refill_counter=refill)
         if L.shape[1]:
             # refilled columns are random: deflate once more and re-orthonormalise
-            Q = Q - L @ (L.conj().T @ Q)
+            Q = deflate(Q, L)
             Q, _, refill = svqb.svqb(Q, seed=seed, refill_counter=refill)
         if extraction == "harmonic":
             theta, V, res, _ = rr.harmonic_ritz(H, Q, 0.5 * (lam_lo + lam_hi))
@@ -152,7 +164,7 @@ def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
                 j = int(np.argmin(np.abs(pth - theta[k])))
                 if res[k] > np.sqrt(eps) * normH and not (pres[j] >= 10.0 * res[k]):
                     ghost[k] = True
-                falling[k] = res[k] <= 0.9 * pres[j]
+                falling[k] = converging(res[k], pres[j])
         acc = inwin & ~ghost
         converged = (bool(acc.any()) or len(lam_L) > 0) and bool(np.all(res[acc] <= eps * normH))
         empty_now = prev is not None and not (acc | (inwin & falling)).any() and not len(lam_L)

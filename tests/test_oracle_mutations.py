@@ -19,6 +19,7 @@ import scipy.linalg
 
 import test_oracle_pins as pins
 from oracle import coeffs, filter as filt, kpm, lattice, mlp, quality, rng, rr, sell, svqb
+from oracle import solve
 
 
 # ---------------------------------------------------------------- mutants
@@ -370,6 +371,23 @@ MUTANTS = {
         _wrap(quality, "effort_linear", lambda o: lambda eta0, S_w, delta, N_T, N_S:
               eta0 * S_w / delta * N_T * (N_S / N_T) / (1.0 - N_T / N_S)),
         [pins.test_effort_model_linear_minimum_at_four_NT]),
+    "empty-window progress without converging pairs": (
+        _wrap(solve, "converging", lambda o: lambda res, prev: False),
+        [pins.test_chebfd_weak_filter_is_not_taken_for_an_empty_window]),
+    "locking without deflation against the locked vectors": (
+        _wrap(solve, "deflate", lambda o: lambda Y, L: Y),
+        [pins.test_chebfd_locking_on_linear_dos,
+         pins.test_chebfd_locking_deflation_over_a_long_run]),
+    "adaptive margin where the search interval holds n_s / 2": (
+        _wrap(solve, "degree_from_moments",
+              lambda o: lambda mu, D, a, b, lo, hi, ns, Np0, **k: o(mu, D, a, b, lo, hi, ns // 2,
+                                                                   Np0, **k)),
+        [pins.test_adaptive_degree_follows_the_linear_dos_rule]),
+    "adaptive degree without N_0": (
+        _wrap(solve, "degree_from_moments",
+              lambda o: lambda *a, **k: (lambda r: (r[0], r[1], max(2, int(round(r[2] / 6.23)))))(
+                  o(*a, **k))),
+        [pins.test_adaptive_degree_follows_the_linear_dos_rule]),
     "MLP gradient of one layer with the wrong sign": (
         _wrap(mlp, "loss_and_grad", _mlp_grad_sign),
         [pins.test_mlp_gradient_matches_central_differences]),

@@ -703,6 +703,29 @@ def test_adaptive_degree_follows_the_linear_dos_rule():
     assert fixed["converged"] and r["n_mvm"] < fixed["n_mvm"]
 
 
+def test_chebfd_locking_deflation_over_a_long_run():
+    """Hard locking with a weak filter and a tight eps (linear-DOS diagonal,
+    D = 4000, N_T = 100, N_S = 200, N_p = 40, eps = 1e-13): pairs lock from
+    the early iterations on and the run goes on for many more.  The locked
+    vectors are accurate only to about eps, so the search block keeps small
+    components along their eigenvectors, which the filter passes while it
+    damps everything outside the window; only the deflation against the
+    locked vectors keeps those components from growing into duplicate Ritz
+    pairs.  The run converges to exactly the 100 window eigenvalues, each
+    once, with orthonormal vectors."""
+    D, NS, Np = 4000, 200, 40
+    delta = np.sqrt(100.0 / D)
+    lam = lattice.linear_dos_eigs(D)
+    H = sp.diags(lam).tocsr()
+    r = solve.chebfd(H, -1.0, 1.0, -delta, delta, NS, Np, 1e-13, complex_values=False,
+                     locking=True, max_iter=40)
+    exact = np.sort(lam[np.abs(lam) <= delta])
+    assert r["converged"] and len(r["theta"]) == len(exact) == 100
+    assert np.abs(np.sort(r["theta"]) - exact).max() <= 1e-12
+    assert np.abs(r["V"].T @ r["V"] - np.eye(100)).max() <= 1e-10
+    assert r["locked"] >= 80
+
+
 def test_chebfd_locking_on_linear_dos():
     """Hard locking (Sec. 6) on the linear-DOS diagonal (D = 4000, window
     +-0.158 with N_T = 100, N_S = 200, N_p = 95): the eigenvalues near the
