@@ -318,3 +318,24 @@ def test_solve_locking_matches_oracle(precision):
     with pytest.raises(pkg.ChebFDError):
         pkg.chebfd_solve(H, -delta, delta, NS, Np, a=-1.0, b=1.0, locking=True,
                          extraction="harmonic")
+
+
+def test_solve_locking_deflation_over_a_long_run():
+    """The oracle pin's long locking run through the C ABI (linear-DOS
+    diagonal, D = 4000, N_S = 200, N_p = 40, eps = 1e-13): pairs lock from the
+    early iterations on and the run goes on for many more, so only the
+    deflation of each filtered block against the locked vectors keeps their
+    leftover components from returning as duplicate pairs.  Exactly the 100
+    window eigenvalues, each once, with orthonormal vectors."""
+    D, NS, Np = 4000, 200, 40
+    delta = np.sqrt(100.0 / D)
+    lam = lattice.linear_dos_eigs(D)
+    H = pkg.chebfd_matrix_create_csr(np.arange(D + 1), np.arange(D), lam)
+    r = pkg.chebfd_solve(H, -delta, delta, NS, Np, eps=1e-13, a=-1.0, b=1.0, locking=True,
+                         max_iter=40)
+    exact = np.sort(lam[np.abs(lam) <= delta])
+    assert r["converged"] and r["nev"] == len(exact) == 100
+    assert np.abs(np.sort(r["lam"]) - exact).max() <= 1e-12
+    V = r["V"].cpu().numpy()
+    assert np.abs(V.T @ V - np.eye(100)).max() <= 1e-10
+    assert max(rec["locked"] for rec in r["log"]) >= 80
