@@ -19,7 +19,7 @@ import scipy.linalg
 
 import test_oracle_pins as pins
 from oracle import coeffs, filter as filt, kpm, lattice, mlp, quality, rng, rr, sell, svqb
-from oracle import solve
+from oracle import bounds, solve
 
 
 # ---------------------------------------------------------------- mutants
@@ -388,6 +388,22 @@ MUTANTS = {
               lambda o: lambda *a, **k: (lambda r: (r[0], r[1], max(2, int(round(r[2] / 6.23)))))(
                   o(*a, **k))),
         [pins.test_adaptive_degree_follows_the_linear_dos_rule]),
+    "KPM without the Jackson damping": (
+        _wrap(kpm, "jackson_kpm", lambda o: lambda M: np.ones(M)),
+        [pins.test_jackson_damped_kpm_dos_is_nonnegative]),
+    "onsite disorder left out": (
+        _wrap(lattice, "disorder", lambda o: lambda seed, count, W: np.zeros(count)),
+        [pins.test_graphene_disorder_on_the_diagonal]),
+    "N_0 table read one row late": (
+        lambda mp: mp.setattr(solve, "TAB_LANCZOS_N0",
+                              solve.TAB_LANCZOS_N0[1:] + (solve.TAB_LANCZOS_N0[-1],)),
+        [pins.test_lanczos_N0_of_the_solver_follows_tab_lanczoskernel]),
+    "residual norms squared": (
+        _wrap(rr, "residual_norms", lambda o: lambda H, V, th: o(H, V, th) ** 2),
+        [pins.test_residual_norms_two_state_closed_form]),
+    "Lanczos bounds not clamped to Gershgorin": (
+        _wrap(bounds, "gershgorin", lambda o: lambda H: (-np.inf, np.inf)),
+        [pins.test_lanczos_bounds_stay_inside_gershgorin]),
     "MLP gradient of one layer with the wrong sign": (
         _wrap(mlp, "loss_and_grad", _mlp_grad_sign),
         [pins.test_mlp_gradient_matches_central_differences]),

@@ -200,6 +200,28 @@ def test_topi_small_lattice_duplicates_summed():
     assert np.array_equal(H.toarray(), big.toarray())
 
 
+def test_graphene_disorder_on_the_diagonal():
+    """Onsite disorder of the graphene generator: W (u - 1/2) per orbital, so
+    the diagonal lies in [-W/2, W/2) with the uniform distribution's spread
+    W / sqrt(12), changes with the seed, and vanishes at W = 0; the hopping
+    entries stay -t whatever W."""
+    Lx, Ly, W = 30, 20, 1.4
+    rp, c, v = lattice.graphene_csr(Lx, Ly, t=1.0, W=W, seed=3)
+    Hs = lattice.to_scipy(rp, c, v)
+    d = Hs.diagonal()
+    n = len(d)
+    assert np.all(d >= -W / 2) and np.all(d < W / 2)
+    assert abs(d.std() - W / np.sqrt(12.0)) <= 0.08 * W / np.sqrt(12.0)
+    assert abs(d.mean()) <= 4 * W / np.sqrt(12.0 * n)
+    off = (Hs - __import__("scipy").sparse.diags(d)).tocsr()
+    off.eliminate_zeros()
+    assert np.all(off.data == -1.0) and off.nnz == 3 * n
+    d2 = lattice.to_scipy(*lattice.graphene_csr(Lx, Ly, t=1.0, W=W, seed=4)).diagonal()
+    assert np.abs(d2 - d).max() > 0.1 * W
+    d0 = lattice.to_scipy(*lattice.graphene_csr(Lx, Ly, t=1.0, W=0.0, seed=3)).diagonal()
+    assert np.all(d0 == 0.0)
+
+
 def test_graphene_structure_and_clean_spectrum():
     rp, c, v = lattice.graphene_csr(6, 9, W=0.0)
     assert np.all(np.diff(rp) == 4)
@@ -320,6 +342,21 @@ def test_tab_lanczoskernel_scaling_constants():
         assert abs(e_opt / 1000.0 - eta0) <= 0.02 * eta0, (c, e_opt)
 
 
+def test_lanczos_N0_of_the_solver_follows_tab_lanczoskernel():
+    """The N_0 the solver's degree rule uses (Sec. 2.4, adaptive degree) is
+    Tab. lanczoskernel's at the printed interval centres, symmetric in the
+    centre, between the neighbouring rows in between, and the last row's
+    beyond c / S_w = 0.9."""
+    rows = [(float(c), float(N0)) for c, N0, _ in _rows("tab_lanczoskernel.txt")]
+    for c, N0 in rows:
+        assert abs(solve.lanczos_N0(c) - N0) <= 1e-12, (c, N0)
+        assert abs(solve.lanczos_N0(-c) - N0) <= 1e-12
+    for (c0, n0), (c1, n1) in zip(rows, rows[1:]):
+        v = solve.lanczos_N0(0.5 * (c0 + c1))
+        assert min(n0, n1) <= v <= max(n0, n1)
+    assert solve.lanczos_N0(0.97) == rows[-1][1]
+
+
 def test_tab_num_optimal_degree_quality_and_effort():
     for dos, NS, dpd, Np, eta, est, num, nit, star in _rows("tab_num.txt")[::2]:
         NS, dpd, Np, eta, est = int(NS), float(dpd), int(Np), float(eta), float(est)
@@ -376,6 +413,27 @@ def test_fig_filtermatrix_weight_bound():
 # ---------------------------------------------------------------- KPM, bounds, SVQB, RR
 
 
+def test_jackson_damped_kpm_dos_is_nonnegative():
+    """The Jackson kernel is a positive kernel: the damped Chebyshev series of
+    a density of states (a sum of delta peaks) is nowhere negative, while the
+    undamped series oscillates below zero (the Gibbs oscillations the damping
+    removes; Sec. 2.1, Tab. Kernel, and the KPM of Sec. 3.1 step 1).  Exact
+    moments of a diagonal matrix, M = 128, on a fine grid."""
+    lam = np.concatenate([np.linspace(-0.9, -0.2, 150), np.linspace(0.3, 0.8, 90)])
+    a, b = -1.0, 1.0
+    x = lam  # alpha = 1, beta = 0
+    M = 128
+    mu = np.cos(np.multiply.outer(np.arange(M), np.arccos(x))).mean(axis=1)
+    grid = np.linspace(-0.999, 0.999, 4001)
+    rho = kpm.dos(mu, len(lam), a, b, grid)
+    assert rho.min() >= -1e-9 * rho.max()
+    rho_plain = kpm.dos(mu, len(lam), a, b, grid, g=np.ones(M))
+    assert rho_plain.min() < -1e-3 * rho_plain.max()
+    # both integrate to the number of states
+    for r in (rho, rho_plain):
+        assert abs(np.trapezoid(r, grid) - len(lam)) <= 0.02 * len(lam)
+
+
 def test_kpm_trace_exact_on_diagonal_and_count():
     lam = lattice.flat_dos_eigs(2000)
     H = sp.diags(lam).tocsr()
@@ -396,6 +454,33 @@ def test_kpm_count_on_lattice_against_dense():
     assert mu[0] == pytest.approx(1.0, abs=1e-12)
     cnt = kpm.count_in_window(mu, H.shape[0], a, b, -1.5, 1.5)
     assert abs(cnt - np.sum(np.abs(e) <= 1.5)) < 12
+
+
+
+def test_residual_norms_two_state_closed_form():
+    """For v = cos(phi) e_1 + e^{i psi} sin(phi) e_2 and H = diag(l1, l2, ...),
+    theta = l1 cos^2 + l2 sin^2 and ||H v - theta v|| = |l1 - l2| |cos sin|
+    (Sec. 3.1 step 7's residual, in closed form)."""
+    import scipy.sparse as sps
+    l = np.array([0.3, -1.1, 2.0, 0.7])
+    H = sps.diags(l.astype(np.complex128)).tocsr()
+    for phi, psi in ((0.0, 0.0), (0.3, 1.0), (np.pi / 4, -2.0), (1.2, 0.5)):
+        v = np.zeros(4, np.complex128)
+        v[0], v[1] = np.cos(phi), np.exp(1j * psi) * np.sin(phi)
+        theta = l[0] * np.cos(phi) ** 2 + l[1] * np.sin(phi) ** 2
+        res = rr.residual_norms(H, v[:, None], [theta])[0]
+        want = abs(l[0] - l[1]) * abs(np.cos(phi) * np.sin(phi))
+        assert abs(res - want) <= 1e-14
+
+
+def test_lanczos_bounds_stay_inside_gershgorin():
+    """The interval of Sec. 3.1 step 1 is widened by a margin but never beyond
+    the Gershgorin discs: for a diagonal matrix the discs are the exact
+    extremes, so [a, b] is exactly [min, max] of its eigenvalues."""
+    lam = np.linspace(-1.0, 1.0, 400)
+    H = lattice.to_scipy(*lattice.diagonal_csr(lam))
+    a, b = bounds.lanczos_bounds(H, 30, seed=0)
+    assert a == -1.0 and b == 1.0
 
 
 @pytest.mark.parametrize("gen", ["topi", "graphene"])
