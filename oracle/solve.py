@@ -94,6 +94,13 @@ def deflate(Y, L):
     return Y - L @ (L.conj().T @ Y)
 
 
+def is_ghost(res, res_prev_nearest, eps, normH):
+    """Ghost test of Sec. 3.1 step 7 (reading): an in-window pair whose
+    residual stays above sqrt(eps) ||H|| without having fallen tenfold since
+    the previous iteration's nearest pair."""
+    return res > np.sqrt(eps) * normH and not (res_prev_nearest >= 10.0 * res)
+
+
 def converging(res, res_prev_nearest):
     """A pair still converging for the empty-window test (reading of Sec. 3.1
     step 8): its residual at most 0.9 of the previous iteration's nearest."""
@@ -162,7 +169,7 @@ def chebfd(H, a, b, lam_lo, lam_hi, ns, Np, eps, kind="lanczos", mu=2.0, seed=0,
             pth, pres = prev
             for k in np.nonzero(inwin)[0]:
                 j = int(np.argmin(np.abs(pth - theta[k])))
-                if res[k] > np.sqrt(eps) * normH and not (pres[j] >= 10.0 * res[k]):
+                if is_ghost(res[k], pres[j], eps, normH):
                     ghost[k] = True
                 falling[k] = converging(res[k], pres[j])
         acc = inwin & ~ghost
